@@ -1,0 +1,54 @@
+/*
+ * Kernel-level entry points of libkfmeg.so: the individual GPU operations
+ * that kf_filter / fis_smooth chain together, exposed so they can be checked
+ * one by one.  Same conventions as kfmeg.h: DEVICE pointers, row-major with
+ * explicit leading dimensions (in elements), work enqueued on `stream`
+ * (a cudaStream_t) and finished before return.  dtype: 0 = float64,
+ * 1 = float32, 2 = float32 data multiplied as split bf16 (hi*hi + hi*lo +
+ * lo*hi) on the tensor cores with float32 accumulation.
+ */
+#ifndef KFMEG_KERNELS_H
+#define KFMEG_KERNELS_H
+
+#include "kfmeg.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* C = alpha * A op(B) + beta * C.  A: M x K.  transB = 1: B is N x K and
+ * op(B) = B^T; transB = 0: B is K x N.  sym = 1 (M == N): only the lower
+ * triangle is computed and mirrored, so C comes out exactly symmetric (the
+ * form of every covariance product in eqns 7, 10 and 13).  dtype 2 needs
+ * transB = 1.  Returns KF_ERR_ARG on bad sizes, KF_ERR_UNSUPPORTED when the
+ * dtype is not available. */
+kf_status kfx_gemm(int32_t dtype, int32_t transB, int32_t sym, int64_t M, int64_t N, int64_t K,
+                   double alpha, const void* A, int64_t lda, const void* B, int64_t ldb,
+                   double beta, void* C, int64_t ldc, void* stream);
+
+/* Cholesky A = L L^T (lower, in place, n x n; the upper triangle outside the
+ * diagonal blocks is untouched), then B <- B A^{-1} = B L^{-T} L^{-1} for the
+ * M x n matrix B (skipped when B is NULL).  This is the solve of the smoother
+ * gain, eqn 11 (J = P_{t|t} F^T P_{t+1|t}^{-1}), and of the Kalman gain, eqn 8
+ * (K = P H^T S^{-1}).  dtype 0 or 1.  A non-positive pivot returns
+ * KF_ERR_NOT_PD with *fail_index = its 0-based index (else -1). */
+kf_status kfx_posv_right(int32_t dtype, int64_t n, void* A, int64_t lda, int64_t M, void* B,
+                         int64_t ldb, int64_t* fail_index, void* stream);
+
+/* out = F P F^T + Q for F in compressed-row form (rowptr: N+1, col/val: nnz),
+ * the mesh-coupled prediction of eqns 2-3 / eqn 7.  dtype 0 or 1 for P / out;
+ * Q per q_kind (kf_cov_kind, float64, NULL allowed with q_kind = -1). */
+kf_status kfx_spmm_fpft(int32_t dtype, int64_t N, const int64_t* rowptr, const int64_t* col,
+                        const double* val, const void* P, int64_t ldp, void* out, int64_t ldo,
+                        int32_t q_kind, const double* Q, void* stream);
+
+/* Splits float32 A (rows x cols) into bf16 planes hi = bf16(A) and
+ * lo = bf16(A - hi) (round to nearest), leading dimension ldh >= cols; the
+ * pad columns are zeroed.  The operand form of the split-bf16 products. */
+kf_status kfx_split_bf16(int64_t rows, int64_t cols, const float* A, int64_t lda, void* hi, void* lo,
+                         int64_t ldh, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KFMEG_KERNELS_H */

@@ -1,0 +1,149 @@
+// Kernel-level C entry points (include/kfmeg_kernels.h).
+#include <vector>
+
+#include "../../include/kfmeg_kernels.h"
+#include "ops.cuh"
+#include "tc_gemm.cuh"
+
+using namespace kfm;
+
+namespace {
+
+template <typename T>
+kf_status gemm_typed(int32_t dtype, int32_t transB, int32_t sym, int64_t M, int64_t N, int64_t K, double alpha,
+                     const void* A, int64_t lda, const void* B, int64_t ldb, double beta, void* C, int64_t ldc,
+                     cudaStream_t s) {
+  GemmParams<T> g;
+  g.M = (int)M; g.N = (int)N; g.K = (int)K;
+  g.A = (const T*)A; g.lda = lda;
+  g.B = (const T*)B; g.ldb = ldb;
+  g.alpha = (T)alpha;
+  if (beta != 0.0) {
+    g.cin = (const T*)C; g.ldcin = ldc; g.beta = (T)beta;
+  }
+  g.out = (T*)C; g.ldo = ldc;
+  g.sym = sym ? 1 : 0;
+  return gemm_simt<T>(s, transB != 0, g);
+}
+
+}  // namespace
+
+extern "C" {
+
+kf_status kfx_gemm(int32_t dtype, int32_t transB, int32_t sym, int64_t M, int64_t N, int64_t K, double alpha,
+                   const void* A, int64_t lda, const void* B, int64_t ldb, double beta, void* C, int64_t ldc,
+                   void* stream) {
+  if (M < 0 || N < 0 || K < 0 || M > INT32_MAX || N > INT32_MAX || K > INT32_MAX) return KF_ERR_ARG;
+  if ((sym && M != N) || !C || (K > 0 && (!A || !B))) return KF_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  kf_status st;
+  if (dtype == 0) {
+    st = gemm_typed<double>(dtype, transB, sym, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s);
+  } else if (dtype == 1) {
+    st = gemm_typed<float>(dtype, transB, sym, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s);
+  } else if (dtype == 2) {
+    if (!transB) return KF_ERR_ARG;
+    if (!tc_available()) return KF_ERR_UNSUPPORTED;
+    GemmParams<float> g;
+    g.M = (int)M; g.N = (int)N; g.K = (int)K;
+    g.A = (const float*)A; g.lda = lda;
+    g.B = (const float*)B; g.ldb = ldb;
+    g.alpha = (float)alpha;
+    if (beta != 0.0) {
+      g.cin = (const float*)C; g.ldcin = ldc; g.beta = (float)beta;
+    }
+    g.out = (float*)C; g.ldo = ldc;
+    g.sym = sym ? 1 : 0;
+    TcScratch sc;
+    std::vector<void*> mem;
+    int64_t rows = M > N ? M : N;
+    int64_t ld = round_up(K > 0 ? K : 1, 64);
+    st = tc_scratch_alloc(sc, rows, ld, [&](void** ptr, size_t bytes) -> kf_status {
+      if (cudaMalloc(ptr, bytes) != cudaSuccess) return KF_ERR_CUDA;
+      mem.push_back(*ptr);
+      return KF_OK;
+    });
+    if (st == KF_OK) st = tc_gemm_bf16x3(s, sc, g);
+    cudaStreamSynchronize(s);
+    for (void* p : mem) cudaFree(p);
+  } else {
+    return KF_ERR_ARG;
+  }
+  if (st != KF_OK) return st;
+  KF_CUDA_TRY(cudaStreamSynchronize(s));
+  return KF_OK;
+}
+
+kf_status kfx_posv_right(int32_t dtype, int64_t n, void* A, int64_t lda, int64_t M, void* B, int64_t ldb,
+                         int64_t* fail_index, void* stream) {
+  if (fail_index) *fail_index = -1;
+  if (n < 1 || n > INT32_MAX || M < 0 || M > INT32_MAX || !A || lda < n) return KF_ERR_ARG;
+  if (B && ldb < n) return KF_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  void* dinv = nullptr;
+  int* st = nullptr;
+  const int nb = dtype == 0 ? potrf_block<double>() : potrf_block<float>();
+  const size_t esz = dtype == 0 ? 8 : 4;
+  if (dtype != 0 && dtype != 1) return KF_ERR_ARG;
+  KF_CUDA_TRY(cudaMalloc(&dinv, (size_t)round_up(n, nb) * nb * esz));
+  if (cudaMalloc(&st, ST_WORDS * sizeof(int)) != cudaSuccess) {
+    cudaFree(dinv);
+    return KF_ERR_CUDA;
+  }
+  cudaMemsetAsync(st, 0, ST_WORDS * sizeof(int), s);
+  kf_status r;
+  if (dtype == 0) {
+    r = potrf<double>(s, (double*)A, lda, (int)n, (double*)dinv, nb, st, 0);
+    if (r == KF_OK && B && M > 0)
+      r = trsm_right<double>(s, true, (int)M, (int)n, (double*)A, lda, (double*)dinv, nb, (double*)B, ldb, st);
+    if (r == KF_OK && B && M > 0)
+      r = trsm_right<double>(s, false, (int)M, (int)n, (double*)A, lda, (double*)dinv, nb, (double*)B, ldb, st);
+  } else {
+    r = potrf<float>(s, (float*)A, lda, (int)n, (float*)dinv, nb, st, 0);
+    if (r == KF_OK && B && M > 0)
+      r = trsm_right<float>(s, true, (int)M, (int)n, (float*)A, lda, (float*)dinv, nb, (float*)B, ldb, st);
+    if (r == KF_OK && B && M > 0)
+      r = trsm_right<float>(s, false, (int)M, (int)n, (float*)A, lda, (float*)dinv, nb, (float*)B, ldb, st);
+  }
+  int h[ST_WORDS] = {0, 0, 0, 0};
+  cudaMemcpyAsync(h, st, sizeof(h), cudaMemcpyDeviceToHost, s);
+  cudaError_t e = cudaStreamSynchronize(s);
+  cudaFree(dinv);
+  cudaFree(st);
+  if (e != cudaSuccess) return KF_ERR_CUDA;
+  if (r != KF_OK) return r;
+  if (h[ST_CODE] && fail_index) *fail_index = h[ST_INDEX];
+  return (kf_status)h[ST_CODE];
+}
+
+kf_status kfx_spmm_fpft(int32_t dtype, int64_t N, const int64_t* rowptr, const int64_t* col, const double* val,
+                        const void* P, int64_t ldp, void* out, int64_t ldo, int32_t q_kind, const double* Q,
+                        void* stream) {
+  if (N < 1 || !rowptr || !col || !val || !P || !out || ldp < N || ldo < N) return KF_ERR_ARG;
+  if (q_kind > 2 || (q_kind >= 0 && !Q)) return KF_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  void* W = nullptr;
+  const size_t esz = dtype == 0 ? 8 : 4;
+  if (dtype != 0 && dtype != 1) return KF_ERR_ARG;
+  KF_CUDA_TRY(cudaMalloc(&W, (size_t)N * N * esz));
+  kf_status r = dtype == 0
+                    ? spmm_fpft<double>(s, N, rowptr, col, val, (const double*)P, ldp, (double*)W, N, (double*)out,
+                                        ldo, q_kind, Q)
+                    : spmm_fpft<float>(s, N, rowptr, col, val, (const float*)P, ldp, (float*)W, N, (float*)out, ldo,
+                                       q_kind, Q);
+  cudaError_t e = cudaStreamSynchronize(s);
+  cudaFree(W);
+  if (e != cudaSuccess) return KF_ERR_CUDA;
+  return r;
+}
+
+kf_status kfx_split_bf16(int64_t rows, int64_t cols, const float* A, int64_t lda, void* hi, void* lo, int64_t ldh,
+                         void* stream) {
+  if (rows < 0 || cols < 0 || ldh < cols || !A || !hi || !lo) return KF_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  KF_TRY(split_bf16(s, rows, cols, A, lda, (__nv_bfloat16*)hi, (__nv_bfloat16*)lo, ldh));
+  KF_CUDA_TRY(cudaStreamSynchronize(s));
+  return KF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,172 @@
+// CUDA-core (FMA) tiled GEMM for float64 and float32 with the fused
+// covariance epilogue of ops.cuh.  Used for every float64 product of the
+// plain path, the float32 path, and the blocked Cholesky / triangular solves.
+#include "ops.cuh"
+
+namespace kfm {
+
+int64_t g_launches = 0;
+
+template <typename T> struct SimtCfg;
+// float64: 64 x 64 tiles, 4 x 4 outputs per thread (the FP64 pipe is the limit).
+template <> struct SimtCfg<double> {
+  static constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4, PAD = 2;
+};
+// float32: 128 x 128 tiles, 8 x 8 outputs per thread.
+template <> struct SimtCfg<float> {
+  static constexpr int BM = 128, BN = 128, BK = 8, TM = 8, TN = 8, PAD = 4;
+};
+
+__device__ __forceinline__ double q_value(int q_kind, const double* q, int64_t ldq, int i, int j) {
+  if (q_kind == 0) return i == j ? q[0] : 0.0;
+  if (q_kind == 1) return i == j ? q[i] : 0.0;
+  if (q_kind == 2) return q[(int64_t)i * ldq + j];
+  return 0.0;
+}
+
+// Maps a linear block index onto the lower-triangular tile (tm >= tn).
+__device__ __forceinline__ void tri_tile(int b, int& tm, int& tn) {
+  int r = (int)((sqrtf(8.0f * (float)b + 1.0f) - 1.0f) * 0.5f);
+  while ((r + 1) * (r + 2) / 2 <= b) ++r;
+  while (r * (r + 1) / 2 > b) --r;
+  tm = r;
+  tn = b - r * (r + 1) / 2;
+}
+
+template <typename T>
+__device__ __forceinline__ void epilogue_store(const GemmParams<T>& p, int gi, int gj, T acc) {
+  T vpre = p.alpha * acc;
+  if (p.cin) vpre += p.beta * p.cin[(int64_t)gi * p.ldcin + gj];
+  T v = vpre;
+  if (p.csub) v -= p.csub[(int64_t)gi * p.ldcsub + gj];
+  const bool mirror = (p.sym == 1) && gi != gj;
+  if (p.out) {
+    p.out[(int64_t)gi * p.ldo + gj] = v;
+    if (mirror) p.out[(int64_t)gj * p.ldo + gi] = v;
+  }
+  if (p.out2) {
+    T w = vpre + (T)q_value(p.q_kind, p.q, p.ldq, gi, gj);
+    p.out2[(int64_t)gi * p.ldo2 + gj] = w;
+    if (mirror) p.out2[(int64_t)gj * p.ldo2 + gi] = w;
+  }
+  if (gi == gj) {
+    if (p.diag_out) p.diag_out[gi] = (double)vpre;
+    if (p.check_diag && !(vpre > T(0) && isfinite((double)vpre)))
+      status_set(p.status, KF_ERR_NUMERIC, p.step, gi);
+  }
+}
+
+template <typename T, bool TB>
+__global__ void __launch_bounds__(256) gemm_simt_kernel(GemmParams<T> p) {
+  using C = SimtCfg<T>;
+  constexpr int BM = C::BM, BN = C::BN, BK = C::BK, TM = C::TM, TN = C::TN;
+  constexpr int LDA_S = BM + C::PAD, LDB_S = BN + C::PAD;
+  __shared__ __align__(16) T As[BK * LDA_S];
+  __shared__ __align__(16) T Bs[BK * LDB_S];
+
+  int tm, tn;
+  if (p.sym) {
+    tri_tile(blockIdx.x, tm, tn);
+  } else {
+    tn = blockIdx.x;
+    tm = blockIdx.y;
+  }
+  if (status_failed(p.status)) return;
+  const int m0 = tm * BM, n0 = tn * BN;
+  const int tid = threadIdx.x;
+  const int tx = tid % 16, ty = tid / 16;
+
+  T acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
+
+  for (int k0 = 0; k0 < p.K; k0 += BK) {
+    // A tile: BM x BK, stored transposed As[kk][row]
+#pragma unroll
+    for (int l = 0; l < (BM * BK) / 256; ++l) {
+      int idx = tid + l * 256;
+      int row = idx / BK, kk = idx % BK;
+      int gr = m0 + row, gk = k0 + kk;
+      T v = T(0);
+      if (gr < p.M && gk < p.K) v = p.A[(int64_t)gr * p.lda + gk];
+      As[kk * LDA_S + row] = v;
+    }
+    if (TB) {
+#pragma unroll
+      for (int l = 0; l < (BN * BK) / 256; ++l) {
+        int idx = tid + l * 256;
+        int col = idx / BK, kk = idx % BK;
+        int gc = n0 + col, gk = k0 + kk;
+        T v = T(0);
+        if (gc < p.N && gk < p.K) v = p.B[(int64_t)gc * p.ldb + gk];
+        Bs[kk * LDB_S + col] = v;
+      }
+    } else {
+#pragma unroll
+      for (int l = 0; l < (BN * BK) / 256; ++l) {
+        int idx = tid + l * 256;
+        int kk = idx / BN, col = idx % BN;
+        int gc = n0 + col, gk = k0 + kk;
+        T v = T(0);
+        if (gc < p.N && gk < p.K) v = p.B[(int64_t)gk * p.ldb + gc];
+        Bs[kk * LDB_S + col] = v;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      T a[TM], b[TN];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) a[i] = As[kk * LDA_S + ty * TM + i];
+#pragma unroll
+      for (int j = 0; j < TN; ++j) b[j] = Bs[kk * LDB_S + tx * TN + j];
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    int gi = m0 + ty * TM + i;
+    if (gi >= p.M) continue;
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      int gj = n0 + tx * TN + j;
+      if (gj >= p.N) continue;
+      if (p.sym && gj > gi) continue;
+      epilogue_store(p, gi, gj, acc[i][j]);
+    }
+  }
+}
+
+template <typename T>
+kf_status gemm_simt(cudaStream_t s, bool transB, const GemmParams<T>& p) {
+  using C = SimtCfg<T>;
+  if (p.M <= 0 || p.N <= 0) return KF_OK;
+  if (p.K < 0) return KF_ERR_ARG;
+  dim3 grid;
+  if (p.sym) {
+    if (p.M != p.N) return KF_ERR_ARG;
+    int64_t nt = ceil_div(p.M, C::BM);
+    grid = dim3((unsigned)(nt * (nt + 1) / 2));
+  } else {
+    grid = dim3((unsigned)ceil_div(p.N, C::BN), (unsigned)ceil_div(p.M, C::BM));
+    if (grid.y > 65535) return KF_ERR_ARG;
+  }
+  if (transB)
+    gemm_simt_kernel<T, true><<<grid, 256, 0, s>>>(p);
+  else
+    gemm_simt_kernel<T, false><<<grid, 256, 0, s>>>(p);
+  ++g_launches;
+  return launch_check("gemm_simt");
+}
+
+template kf_status gemm_simt<double>(cudaStream_t, bool, const GemmParams<double>&);
+template kf_status gemm_simt<float>(cudaStream_t, bool, const GemmParams<float>&);
+
+}  // namespace kfm

@@ -1,0 +1,126 @@
+// Internal (non-ABI) launchers shared by the plan executor and the kernel-level
+// entry points.  All matrices are row-major with an explicit leading dimension.
+#pragma once
+
+#include "common.cuh"
+
+namespace kfm {
+
+// Epilogue shared by every GEMM flavour.  With acc = sum_k A[i,k] op(B)[k,j]:
+//   v_pre = alpha * acc + beta * cin[i,j]          (cin optional)
+//   v     = v_pre - csub[i,j]                      (csub optional)
+//   out[i,j]  = v                                  (out optional)
+//   out2[i,j] = v_pre + Q[i,j]                     (out2 optional; Q per q_kind,
+//                                                   q_kind < 0: no Q)
+//   diag_out[i] = v_pre at i == j                  (optional, float64)
+// sym == 1: M == N, only tiles on or below the diagonal are computed and each
+// written element (i >= j) is mirrored to (j, i), so outputs are exactly
+// symmetric.  sym == 2: as 1 but without the mirror (lower triangle only).  check_diag != 0: a diagonal v_pre that is not finite and > 0
+// sets KF_ERR_NUMERIC in status with the given step.
+template <typename T>
+struct GemmParams {
+  int M = 0, N = 0, K = 0;
+  const T* A = nullptr;
+  int64_t lda = 0;
+  const T* B = nullptr;
+  int64_t ldb = 0;
+  T alpha = T(1);
+  const T* cin = nullptr;
+  int64_t ldcin = 0;
+  T beta = T(0);
+  const T* csub = nullptr;
+  int64_t ldcsub = 0;
+  T* out = nullptr;
+  int64_t ldo = 0;
+  T* out2 = nullptr;
+  int64_t ldo2 = 0;
+  int q_kind = -1;
+  const double* q = nullptr;
+  int64_t ldq = 0;
+  double* diag_out = nullptr;
+  int* status = nullptr;
+  int check_diag = 0;
+  int step = 0;
+  int sym = 0;
+};
+
+// C = op(A) x op(B) with A: M x K row-major; B: N x K row-major when transB
+// (C = A B^T) else K x N row-major (C = A B).  Plain CUDA-core FMA tiles.
+template <typename T>
+kf_status gemm_simt(cudaStream_t s, bool transB, const GemmParams<T>& p);
+
+// Blocked right-looking Cholesky A = L L^T of the n x n lower triangle (in
+// place; the strict upper triangle is left untouched).  dinv receives the
+// inverses of the nb x nb diagonal blocks of L (ceil(n/nb) blocks of nb*nb,
+// each row-major with leading dimension nb).  A pivot that is not > 0 sets
+// KF_ERR_NOT_PD in status (step, pivot index) and stops the factorisation.
+template <typename T>
+kf_status potrf(cudaStream_t s, T* A, int64_t lda, int n, T* dinv, int nb, int* status, int step);
+
+template <typename T>
+int potrf_block();  // the nb used by potrf for dtype T
+
+// B <- B L^{-T} (trans = true) or B <- B L^{-1} (trans = false), B: M x n,
+// L: n x n lower triangular from potrf with its diagonal-block inverses dinv.
+template <typename T>
+kf_status trsm_right(cudaStream_t s, bool trans, int M, int n, const T* L, int64_t ldl,
+                     const T* dinv, int nb, T* B, int64_t ldb, int* status);
+
+// ---------------------------------------------------------------- small ops
+
+// dst[i, j] = (Tdst) src[i, j] for i < rows, j < cols; pad columns cols..ld_dst-1 zeroed
+// when zero_pad.
+template <typename Tdst, typename Tsrc>
+kf_status copy2d(cudaStream_t s, Tdst* dst, int64_t ldd, const Tsrc* src, int64_t lds,
+                 int64_t rows, int64_t cols, bool zero_pad = false);
+
+// dst = src + Q (Q per q_kind, q_kind < 0: none), dst may alias src.
+template <typename Tdst, typename Tsrc>
+kf_status add_cov(cudaStream_t s, Tdst* dst, int64_t ldd, const Tsrc* src, int64_t lds, int64_t n,
+                  int q_kind, const double* q);
+
+// y[i] = sum_j A[i, j] x[j] (float64 accumulate); y = ybase + sign * A x when ybase.
+template <typename T>
+kf_status gemv(cudaStream_t s, int64_t rows, int64_t cols, const T* A, int64_t lda,
+               const double* x, const double* ybase, double sign, double* y);
+
+// d[i] = a[i] - b[i]
+kf_status vsub(cudaStream_t s, int64_t n, const double* a, const double* b, double* d);
+
+// innovation: nu = y - H x (m values); non-finite y or nu sets KF_ERR_NUMERIC.
+kf_status innovation(cudaStream_t s, int64_t m, int64_t N, const double* H, const double* x,
+                     const double* y, double* nu, int* status, int step);
+
+// S = H U^T-product + R (m x m, float64), summing float64 partials from
+// split-K chunks of  sum_k H[i, k] Ut[k, j]  (H: m x N float64, Ut: N x m of T).
+template <typename T>
+kf_status innovation_cov(cudaStream_t s, int m, int N, const double* H, int64_t ldh, const T* Ut,
+                         int64_t ldu, int r_kind, const double* R, double* S, int64_t lds,
+                         double* partials, int splits);
+
+// Mean prediction x_out = F x (F per f_kind; identity copies).
+kf_status predict_mean(cudaStream_t s, int f_kind, int64_t N, const double* F,
+                       const int64_t* rowptr, const int64_t* col, const double* x, double* x_out);
+
+// Mesh coupling: out = F P F^T + Q for CSR F (P symmetric, N x N), via
+// W = F P (row combinations) then out = W F^T (gathers within each row of W).
+template <typename T>
+kf_status spmm_fpft(cudaStream_t s, int64_t N, const int64_t* rowptr, const int64_t* col,
+                    const double* val, const T* P, int64_t ldp, T* W, int64_t ldw, T* out,
+                    int64_t ldo, int q_kind, const double* q);
+
+// B = P F^T for CSR F (B[i, j] = sum_k P[i, k] F[j, k]).
+template <typename T>
+kf_status spmm_pft(cudaStream_t s, int64_t N, const int64_t* rowptr, const int64_t* col,
+                   const double* val, const T* P, int64_t ldp, T* out, int64_t ldo);
+
+// Splits float A (rows x cols, lda) into bf16 planes hi = bf16(A), lo = bf16(A - hi);
+// columns cols..ldh-1 of both planes are zeroed.
+kf_status split_bf16(cudaStream_t s, int64_t rows, int64_t cols, const float* A, int64_t lda,
+                     __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t ldh);
+
+// diag_out[i] = A[i, i]
+template <typename T>
+kf_status diag_extract(cudaStream_t s, int64_t n, const T* A, int64_t lda, double* diag_out);
+
+}  // namespace kfm

@@ -1,0 +1,763 @@
+// Plan / executor behind the C ABI of include/kfmeg.h.
+//
+// One plan = one epoch shape (N, m, T) with its precision mode.  It owns:
+//  - the working covariance P (bulk dtype, N x ldN with ldN = N rounded up
+//    to 128 so every row starts 16-byte aligned),
+//  - the covariance store of P_{t|t} (slot 0 holds P0), either complete or as
+//    checkpoints every c steps plus one segment buffer, the skipped steps
+//    being recomputed forward during the smoother (the covariance recursion
+//    does not depend on the data),
+//  - the filter's small buffers (U^T = P H^T, the gain K, S and its factor),
+//  - the smoother's buffers (factor of P_{t+1|t}, J_t, W = J_t D, D), and
+//  - plan-owned copies of F, Q, H, R so fis_smooth needs no caller input.
+// Every time step is a fixed launch sequence on the plan's stream; a device
+// status word is read once at the end of kf_filter / fis_smooth.
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "ops.cuh"
+#include "tc_gemm.cuh"
+
+using namespace kfm;
+
+namespace {
+
+enum Bulk { BULK_F64 = 0, BULK_F32 = 1, BULK_BF16X3 = 2 };
+
+struct ProfMark {
+  int cls;
+  cudaEvent_t a, b;
+};
+
+constexpr int kSplitsS = 8;  // split-K factor of S = H U^T
+
+}  // namespace
+
+struct kf_plan_s {
+  kf_desc d{};
+  cudaStream_t s = nullptr;
+  int64_t N = 0, m = 0, T = 0, ldN = 0, ldm = 0;
+  int bulk = 0, solve = 0;
+  size_t b = 8, sb = 8;   // bytes per bulk / solve element
+  int64_t ckpt = 1;       // 1 = every P_{t|t} stored
+  int64_t nck = 0;        // checkpoint slots
+  int64_t seg_id = -1;    // segment currently held by the segment buffer
+  size_t slot = 0;        // bytes of one N x ldN bulk matrix
+  std::vector<void*> allocs;
+
+  char* store = nullptr;
+  char* seg = nullptr;
+  double *xpred = nullptr, *xfilt = nullptr, *xs = nullptr, *nu = nullptr, *dx = nullptr;
+  char *P = nullptr, *Ut = nullptr, *KV = nullptr, *VK = nullptr, *Hb = nullptr, *tmpN = nullptr;
+  char *Fb = nullptr, *S0b = nullptr;
+  double *S = nullptr, *S0 = nullptr, *Sdinv = nullptr, *partials = nullptr;
+  char *Sl = nullptr, *Sldinv = nullptr;
+  char *Lb = nullptr, *Ldinv = nullptr, *Jb = nullptr;
+  char *Jm = nullptr, *Wb = nullptr, *Db = nullptr, *Pn = nullptr;
+  TcScratch tc{};
+  double *F = nullptr, *Q = nullptr, *H = nullptr, *R = nullptr;
+  int64_t *Frp = nullptr, *Fcol = nullptr;
+  int* status = nullptr;
+  int* status_h = nullptr;
+  bool filtered = false;
+  // staging for kf_solve_host (allocated on first use)
+  double *hY = nullptr, *hx0 = nullptr, *hP0 = nullptr, *hQ = nullptr, *hH = nullptr, *hR = nullptr,
+         *hF = nullptr, *hxf = nullptr, *hdf = nullptr, *hxs = nullptr, *hds = nullptr;
+  int64_t *hFrp = nullptr, *hFcol = nullptr;
+  // profiling
+  bool prof = false;
+  std::vector<ProfMark> marks;
+  std::vector<cudaEvent_t> pool;
+  int64_t launches0 = 0;
+
+  char* slot_ptr(int64_t t) {
+    if (ckpt == 1) return store + (size_t)t * slot;
+    if (t % ckpt == 0) return store + (size_t)(t / ckpt) * slot;
+    return seg + (size_t)(t % ckpt - 1) * slot;
+  }
+};
+
+namespace {
+
+size_t cov_count(int kind, int64_t n) { return kind == 0 ? 1 : kind == 1 ? (size_t)n : (size_t)n * n; }
+
+struct Sizes {
+  uint64_t workspace = 0, slot = 0;
+  int64_t ldN = 0, ldm = 0;
+  size_t b = 8, sb = 8;
+};
+
+Sizes sizes_for(const kf_desc* d) {
+  Sizes z;
+  z.b = d->prec == KF_PREC_FP64 ? 8 : 4;
+  z.sb = (d->prec == KF_PREC_FP64 || d->solve_prec == KF_SOLVE_FP64) ? 8 : 4;
+  z.ldN = round_up(d->N, 128);
+  z.ldm = round_up(d->m, 64);
+  const uint64_t N = d->N, m = d->m, T = d->T, ldN = z.ldN, ldm = z.ldm;
+  z.slot = N * ldN * z.b;
+  uint64_t w = 0;
+  w += 2 * z.slot;                          // P, tmpN
+  w += N * ldm * z.b;                       // Ut
+  w += 2 * N * 2 * ldm * z.b;               // KV, VK
+  w += m * ldN * z.b;                       // Hb
+  w += 2 * m * m * 8 + round_up(m, 64) * 64 * 8 + kSplitsS * m * m * 8;  // S, S0, Sdinv, partials
+  w += (m * m + round_up(m, 64) * 64) * z.b + m * m * z.b;               // Sl, Sldinv, S0b
+  const int64_t nbs = z.sb == 8 ? 64 : 128;
+  w += 2 * N * ldN * z.sb + round_up(N, nbs) * nbs * z.sb;                 // Lb, Jb, Ldinv
+  w += (z.sb != z.b ? z.slot : 0) + 3 * z.slot;                            // Jm, Wb, Db, Pn
+  w += 3 * (T + 1) * N * 8 + m * 8 + N * 8;                                // means
+  if (d->f_kind == KF_F_CSR) w += d->f_nnz * 16 + (N + 1) * 8;
+  if (d->f_kind == KF_F_DENSE) w += N * N * 8 + z.slot;
+  w += cov_count(d->q_kind, N) * 8 + m * N * 8 + cov_count(d->r_kind, m) * 8;
+  if (d->prec == KF_PREC_MIXED_BF16X3) w += tc_scratch_bytes(N, ldN);
+  w += 4096;
+  z.workspace = w;
+  return z;
+}
+
+kf_status validate(const kf_desc* d) {
+  if (!d) return KF_ERR_ARG;
+  if (d->N < 1 || d->m < 1 || d->T < 1) return KF_ERR_ARG;
+  if (d->N > (1ll << 30) || d->m > (1ll << 20) || d->T > (1ll << 30)) return KF_ERR_ARG;
+  if (d->f_kind < 0 || d->f_kind > 2) return KF_ERR_ARG;
+  if (d->f_kind == KF_F_CSR && d->f_nnz < 1) return KF_ERR_ARG;
+  if (d->prec < 0 || d->prec > 2) return KF_ERR_ARG;
+  if (d->solve_prec < 0 || d->solve_prec > 1) return KF_ERR_ARG;
+  if (d->q_kind < 0 || d->q_kind > 2 || d->r_kind < 0 || d->r_kind > 2) return KF_ERR_ARG;
+  if (d->joseph_every < 0 || d->checkpoint_every < 0) return KF_ERR_ARG;
+  return KF_OK;
+}
+
+kf_status choose_checkpoint(const kf_desc* d, const Sizes& z, int64_t* c_out, uint64_t* store_out) {
+  const int64_t T = d->T;
+  auto store_bytes = [&](int64_t c) -> uint64_t {
+    if (c <= 1) return (uint64_t)(T + 1) * z.slot;
+    return (uint64_t)(T / c + 1 + c - 1) * z.slot;
+  };
+  if (d->checkpoint_every > 0) {
+    int64_t c = d->checkpoint_every > T ? T : d->checkpoint_every;
+    if (c < 1) c = 1;
+    *c_out = c;
+    *store_out = store_bytes(c);
+    if (d->mem_budget_bytes && z.workspace + *store_out > d->mem_budget_bytes) return KF_ERR_BUDGET;
+    return KF_OK;
+  }
+  if (!d->mem_budget_bytes || z.workspace + store_bytes(1) <= d->mem_budget_bytes) {
+    *c_out = 1;
+    *store_out = store_bytes(1);
+    return KF_OK;
+  }
+  int64_t best = -1;
+  uint64_t best_bytes = 0;
+  for (int64_t c = 2; c <= T; ++c) {
+    uint64_t sbytes = store_bytes(c);
+    if (best < 0 || sbytes < best_bytes) {
+      best = c;
+      best_bytes = sbytes;
+    }
+  }
+  if (best < 0 || z.workspace + best_bytes > d->mem_budget_bytes) return KF_ERR_BUDGET;
+  *c_out = best;
+  *store_out = best_bytes;
+  return KF_OK;
+}
+
+template <typename X>
+kf_status dalloc(kf_plan_s* p, X** out, size_t bytes) {
+  void* ptr = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(&ptr, bytes);
+  if (e != cudaSuccess) {
+    fprintf(stderr, "kfmeg: cudaMalloc(%zu) failed: %s\n", bytes, cudaGetErrorString(e));
+    cudaGetLastError();
+    return KF_ERR_CUDA;
+  }
+  p->allocs.push_back(ptr);
+  KF_CUDA_TRY(cudaMemsetAsync(ptr, 0, bytes, p->s));
+  *out = reinterpret_cast<X*>(ptr);
+  return KF_OK;
+}
+
+// ------------------------------------------------------------ profiling
+
+struct Prof {
+  kf_plan_s* p;
+  int cls;
+  cudaEvent_t a = nullptr, b = nullptr;
+  Prof(kf_plan_s* plan, int c) : p(plan), cls(c) {
+    if (!p->prof) return;
+    a = take();
+    b = take();
+    cudaEventRecord(a, p->s);
+  }
+  ~Prof() {
+    if (!p->prof || !a) return;
+    cudaEventRecord(b, p->s);
+    p->marks.push_back({cls, a, b});
+  }
+  cudaEvent_t take() {
+    if (!p->pool.empty()) {
+      cudaEvent_t e = p->pool.back();
+      p->pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+  }
+};
+
+// ------------------------------------------------------------ GEMM dispatch
+
+template <typename B>
+kf_status gemm_bulk(kf_plan_s* p, bool transB, const GemmParams<B>& g);
+
+template <>
+kf_status gemm_bulk<double>(kf_plan_s* p, bool transB, const GemmParams<double>& g) {
+  return gemm_simt<double>(p->s, transB, g);
+}
+
+template <>
+kf_status gemm_bulk<float>(kf_plan_s* p, bool transB, const GemmParams<float>& g) {
+  if (p->bulk == BULK_BF16X3 && transB) return tc_gemm_bf16x3(p->s, p->tc, g);
+  return gemm_simt<float>(p->s, transB, g);
+}
+
+// ------------------------------------------------------------ predict
+
+template <typename B>
+kf_status predict_cov(kf_plan_s* p, const B* src, B* dst) {
+  Prof pr(p, KF_KC_PREDICT);
+  const int64_t N = p->N;
+  if (p->d.f_kind == KF_F_IDENTITY)
+    return add_cov<B, B>(p->s, dst, p->ldN, src, p->ldN, N, p->d.q_kind, p->Q);
+  if (p->d.f_kind == KF_F_CSR)
+    return spmm_fpft<B>(p->s, N, p->Frp, p->Fcol, p->F, src, p->ldN, (B*)p->tmpN, p->ldN, dst, p->ldN,
+                        p->d.q_kind, p->Q);
+  GemmParams<B> g;  // W = F src
+  g.M = (int)N; g.N = (int)N; g.K = (int)N;
+  g.A = (const B*)p->Fb; g.lda = p->ldN;
+  g.B = src; g.ldb = p->ldN;
+  g.out = (B*)p->tmpN; g.ldo = p->ldN;
+  g.status = p->status;
+  KF_TRY(gemm_simt<B>(p->s, false, g));
+  GemmParams<B> h;  // dst = W F^T + Q
+  h.M = (int)N; h.N = (int)N; h.K = (int)N;
+  h.A = (const B*)p->tmpN; h.lda = p->ldN;
+  h.B = (const B*)p->Fb; h.ldb = p->ldN;
+  h.out2 = dst; h.ldo2 = p->ldN;
+  h.q_kind = p->d.q_kind; h.q = p->Q; h.ldq = N;
+  h.status = p->status;
+  return gemm_simt<B>(p->s, true, h);
+}
+
+// ------------------------------------------------------------ filter step
+
+// Covariance part of one filter step t (and the mean update when y != NULL):
+// uses the working P = P_{t|t-1}, writes P_{t|t} to its store slot and
+// leaves P_{t+1|t} in the working P.
+template <typename B>
+kf_status filter_step(kf_plan_s* p, int64_t t, const double* y, double* diag_out) {
+  cudaStream_t s = p->s;
+  const int N = (int)p->N, m = (int)p->m;
+  const int64_t ldN = p->ldN, ldm = p->ldm, ldkv = 2 * p->ldm;
+  B* P = (B*)p->P;
+  B* Ut = (B*)p->Ut;
+  B* KV = (B*)p->KV;
+  {
+    Prof pr(p, KF_KC_INNOVATION);
+    GemmParams<B> g;  // U^T = P H^T  (N x m)
+    g.M = N; g.N = m; g.K = N;
+    g.A = P; g.lda = ldN;
+    g.B = (const B*)p->Hb; g.ldb = ldN;
+    g.out = Ut; g.ldo = ldm;
+    g.status = p->status;
+    KF_TRY(gemm_bulk<B>(p, true, g));
+  }
+  // S = H U^T + R (float64), then its Cholesky factor in place
+  KF_TRY(innovation_cov<B>(s, m, N, p->H, N, Ut, ldm, p->d.r_kind, p->R, p->S, m, p->partials, kSplitsS));
+  const bool joseph = p->d.joseph_every > 0 && (t % p->d.joseph_every) == 0;
+  if (joseph) KF_CUDA_TRY(cudaMemcpyAsync(p->S0, p->S, (size_t)m * m * 8, cudaMemcpyDeviceToDevice, s));
+  const int nbS = potrf_block<double>();
+  KF_TRY(potrf<double>(s, p->S, m, m, p->Sdinv, nbS, p->status, (int)t));
+  const B* L = (const B*)p->S;
+  const B* Ld = (const B*)p->Sdinv;
+  if (sizeof(B) != sizeof(double)) {
+    KF_TRY((copy2d<B, double>(s, (B*)p->Sl, m, p->S, m, m, m)));
+    KF_TRY((copy2d<B, double>(s, (B*)p->Sldinv, nbS, p->Sdinv, nbS, round_up(m, nbS), nbS)));
+    L = (const B*)p->Sl;
+    Ld = (const B*)p->Sldinv;
+  }
+  // K = U^T S^{-1} = U^T L^{-T} L^{-1}, in the left half of KV
+  KF_TRY((copy2d<B, B>(s, KV, ldkv, Ut, ldm, N, m)));
+  KF_TRY(trsm_right<B>(s, true, N, m, L, m, Ld, nbS, KV, ldkv, p->status));
+  KF_TRY(trsm_right<B>(s, false, N, m, L, m, Ld, nbS, KV, ldkv, p->status));
+  if (y) {
+    KF_TRY(innovation(s, m, N, p->H, p->xpred + t * N, y, p->nu, p->status, (int)t));
+    KF_TRY(gemv<B>(s, N, m, KV, ldkv, p->nu, p->xpred + t * N, 1.0, p->xfilt + t * N));
+  }
+  const bool ident = p->d.f_kind == KF_F_IDENTITY;
+  B* dst = (B*)p->slot_ptr(t);
+  GemmParams<B> u;  // P_{t|t} = P - K U  (symmetric by construction), P <- P_{t|t} + Q when F = I
+  u.M = N; u.N = N;
+  u.A = KV; u.lda = ldkv;
+  u.alpha = B(-1);
+  u.cin = P; u.ldcin = ldN; u.beta = B(1);
+  u.out = dst; u.ldo = ldN;
+  if (ident) {
+    u.out2 = P; u.ldo2 = ldN;
+    u.q_kind = p->d.q_kind; u.q = p->Q; u.ldq = N;
+  }
+  u.diag_out = diag_out;
+  u.check_diag = 1;
+  u.step = (int)t;
+  u.status = p->status;
+  u.sym = 1;
+  if (joseph) {
+    // Joseph form (I - KH) P (I - KH)^T + K R K^T = P - K V^T - V K^T with
+    // V = U^T - K S / 2: one rank-2m product [K V][V K]^T.
+    KF_TRY((copy2d<B, double>(s, (B*)p->S0b, m, p->S0, m, m, m)));
+    GemmParams<B> v;
+    v.M = N; v.N = m; v.K = m;
+    v.A = KV; v.lda = ldkv;
+    v.B = (const B*)p->S0b; v.ldb = m;
+    v.alpha = B(-0.5);
+    v.cin = Ut; v.ldcin = ldm; v.beta = B(1);
+    v.out = KV + ldm; v.ldo = ldkv;
+    v.status = p->status;
+    KF_TRY(gemm_simt<B>(s, true, v));
+    B* VK = (B*)p->VK;
+    KF_TRY((copy2d<B, B>(s, VK, ldkv, KV + ldm, ldkv, N, m)));
+    KF_TRY((copy2d<B, B>(s, VK + ldm, ldkv, KV, ldkv, N, m)));
+    u.K = (int)ldkv;
+    u.B = VK; u.ldb = ldkv;
+  } else {
+    u.K = p->bulk == BULK_BF16X3 ? (int)ldm : m;
+    u.B = Ut; u.ldb = ldm;
+  }
+  {
+    Prof pr(p, KF_KC_FILTER_UPDATE);
+    KF_TRY(gemm_bulk<B>(p, true, u));
+  }
+  if (!ident) KF_TRY(predict_cov<B>(p, dst, P));
+  return KF_OK;
+}
+
+template <typename B>
+kf_status recompute_segment(kf_plan_s* p, int64_t k) {
+  const int64_t c = p->ckpt, t0 = k * c, t1 = std::min<int64_t>(t0 + c - 1, p->T);
+  KF_TRY(predict_cov<B>(p, (const B*)p->slot_ptr(t0), (B*)p->P));
+  for (int64_t t = t0 + 1; t <= t1; ++t) KF_TRY(filter_step<B>(p, t, nullptr, nullptr));
+  p->seg_id = k;
+  return KF_OK;
+}
+
+template <typename B>
+kf_status get_P(kf_plan_s* p, int64_t t, const B** out) {
+  if (p->ckpt > 1 && t % p->ckpt != 0 && p->seg_id != t / p->ckpt) KF_TRY(recompute_segment<B>(p, t / p->ckpt));
+  *out = (const B*)p->slot_ptr(t);
+  return KF_OK;
+}
+
+kf_status read_status(kf_plan_s* p, int64_t* fail_step) {
+  KF_CUDA_TRY(cudaMemcpyAsync(p->status_h, p->status, ST_WORDS * sizeof(int), cudaMemcpyDeviceToHost, p->s));
+  KF_CUDA_TRY(cudaStreamSynchronize(p->s));
+  if (fail_step) *fail_step = p->status_h[ST_CODE] ? p->status_h[ST_STEP] : 0;
+  return (kf_status)p->status_h[ST_CODE];
+}
+
+template <typename B>
+kf_status run_filter(kf_plan_s* p, const double* Y, const double* x0, const double* P0, double* x_filt,
+                     double* diagP_filt, int64_t* fail_step) {
+  cudaStream_t s = p->s;
+  const int64_t N = p->N, m = p->m, T = p->T;
+  KF_CUDA_TRY(cudaMemsetAsync(p->status, 0, ST_WORDS * sizeof(int), s));
+  KF_CUDA_TRY(cudaMemcpyAsync(p->xfilt, x0, N * 8, cudaMemcpyDeviceToDevice, s));
+  // P0 into store slot 0 (bulk dtype), then P_{1|0}
+  KF_TRY((copy2d<B, double>(s, (B*)p->slot_ptr(0), p->ldN, P0, N, N, N)));
+  KF_TRY(predict_cov<B>(p, (const B*)p->slot_ptr(0), (B*)p->P));
+  for (int64_t t = 1; t <= T; ++t) {
+    KF_TRY(predict_mean(s, p->d.f_kind, N, p->F, p->Frp, p->Fcol, p->xfilt + (t - 1) * N, p->xpred + t * N));
+    KF_TRY(filter_step<B>(p, t, Y + (t - 1) * m, diagP_filt ? diagP_filt + (t - 1) * N : nullptr));
+    if (p->ckpt > 1 && t % p->ckpt != 0) p->seg_id = t / p->ckpt;
+  }
+  KF_CUDA_TRY(cudaMemcpyAsync(x_filt, p->xfilt + N, (size_t)T * N * 8, cudaMemcpyDeviceToDevice, s));
+  return read_status(p, fail_step);
+}
+
+template <typename B, typename V>
+kf_status run_smoother(kf_plan_s* p, double* x_smooth, double* diagP_smooth, double* P_full, int64_t t_full,
+                       int64_t* fail_step) {
+  cudaStream_t s = p->s;
+  const int64_t N = p->N, T = p->T, ldN = p->ldN;
+  const int nbs = potrf_block<V>();
+  KF_CUDA_TRY(cudaMemsetAsync(p->status, 0, ST_WORDS * sizeof(int), s));
+  B* Pn = (B*)p->Pn;
+  B* Db = (B*)p->Db;
+  B* Wb = (B*)p->Wb;
+  V* Lb = (V*)p->Lb;
+  V* Jb = (V*)p->Jb;
+  B* Jm = sizeof(V) == sizeof(B) ? (B*)p->Jb : (B*)p->Jm;
+  // t = T: smoothed = filtered
+  KF_CUDA_TRY(cudaMemcpyAsync(p->xs + T * N, p->xfilt + T * N, N * 8, cudaMemcpyDeviceToDevice, s));
+  const B* PT;
+  if (T >= 2) {
+    const B* Ptm1;
+    KF_TRY(get_P<B>(p, T - 1, &Ptm1));
+    KF_TRY(predict_cov<B>(p, Ptm1, Pn));
+  }
+  KF_TRY(get_P<B>(p, T, &PT));
+  if (diagP_smooth) KF_TRY(diag_extract<B>(s, N, PT, ldN, diagP_smooth + (T - 1) * N));
+  if (P_full && t_full == T) KF_TRY((copy2d<double, B>(s, P_full, N, PT, ldN, N, N)));
+  if (T >= 2) {
+    GemmParams<B> g;  // D_T = P_{T|T} - P_{T|T-1}  (K = 0 product: epilogue only)
+    g.M = (int)N; g.N = (int)N; g.K = 0;
+    g.cin = PT; g.ldcin = ldN; g.beta = B(1);
+    g.csub = Pn; g.ldcsub = ldN;
+    g.out = Db; g.ldo = ldN;
+    g.sym = 1;
+    g.status = p->status;
+    KF_TRY(gemm_simt<B>(s, true, g));
+  }
+  for (int64_t t = T - 1; t >= 1; --t) {
+    const B* Pt;
+    {
+      Prof pr(p, KF_KC_SMOOTH_SOLVE);
+      // P_{t+1|t} = L L^T
+      KF_TRY((copy2d<V, B>(s, Lb, ldN, Pn, ldN, N, N)));
+      KF_TRY(potrf<V>(s, Lb, ldN, (int)N, (V*)p->Ldinv, nbs, p->status, (int)(t + 1)));
+      KF_TRY(get_P<B>(p, t, &Pt));
+      // J_t = P_{t|t} F^T L^{-T} L^{-1}
+      if (p->d.f_kind == KF_F_IDENTITY) {
+        KF_TRY((copy2d<V, B>(s, Jb, ldN, Pt, ldN, N, N)));
+      } else if (p->d.f_kind == KF_F_CSR) {
+        KF_TRY(spmm_pft<B>(s, N, p->Frp, p->Fcol, p->F, Pt, ldN, (B*)p->tmpN, ldN));
+        KF_TRY((copy2d<V, B>(s, Jb, ldN, (const B*)p->tmpN, ldN, N, N)));
+      } else {
+        GemmParams<B> f;
+        f.M = (int)N; f.N = (int)N; f.K = (int)N;
+        f.A = Pt; f.lda = ldN;
+        f.B = (const B*)p->Fb; f.ldb = ldN;
+        f.out = (B*)p->tmpN; f.ldo = ldN;
+        f.status = p->status;
+        KF_TRY(gemm_simt<B>(s, true, f));
+        KF_TRY((copy2d<V, B>(s, Jb, ldN, (const B*)p->tmpN, ldN, N, N)));
+      }
+      KF_TRY(trsm_right<V>(s, true, (int)N, (int)N, Lb, ldN, (const V*)p->Ldinv, nbs, Jb, ldN, p->status));
+      KF_TRY(trsm_right<V>(s, false, (int)N, (int)N, Lb, ldN, (const V*)p->Ldinv, nbs, Jb, ldN, p->status));
+    }
+    // x_{t|T} = x_{t|t} + J_t (x_{t+1|T} - x_{t+1|t})
+    KF_TRY(vsub(s, N, p->xs + (t + 1) * N, p->xpred + (t + 1) * N, p->dx));
+    KF_TRY(gemv<V>(s, N, N, Jb, ldN, p->dx, p->xfilt + t * N, 1.0, p->xs + t * N));
+    if ((void*)Jm != (void*)Jb) KF_TRY((copy2d<B, V>(s, Jm, ldN, Jb, ldN, N, N)));
+    {
+      Prof pr(p, KF_KC_SMOOTH_GEMM);
+      GemmParams<B> w;  // W = J_t D_{t+1}  (D symmetric)
+      w.M = (int)N; w.N = (int)N; w.K = (int)N;
+      w.A = Jm; w.lda = ldN;
+      w.B = Db; w.ldb = ldN;
+      w.out = Wb; w.ldo = ldN;
+      w.status = p->status;
+      KF_TRY(gemm_bulk<B>(p, true, w));
+    }
+    const B* Ptm1;
+    KF_TRY(get_P<B>(p, t - 1, &Ptm1));
+    KF_TRY(predict_cov<B>(p, Ptm1, Pn));  // P_{t|t-1}
+    {
+      Prof pr(p, KF_KC_SMOOTH_GEMM);
+      GemmParams<B> g;  // D_t = P_{t|t} + W J_t^T - P_{t|t-1};  diag(P_{t|T}) out
+      g.M = (int)N; g.N = (int)N; g.K = (int)N;
+      g.A = Wb; g.lda = ldN;
+      g.B = Jm; g.ldb = ldN;
+      g.cin = Pt; g.ldcin = ldN; g.beta = B(1);
+      g.csub = Pn; g.ldcsub = ldN;
+      g.out = Db; g.ldo = ldN;
+      if (P_full && t_full == t) {
+        g.out2 = (B*)p->tmpN; g.ldo2 = ldN;
+      }
+      g.diag_out = diagP_smooth ? diagP_smooth + (t - 1) * N : nullptr;
+      g.check_diag = 1;
+      g.step = (int)t;
+      g.sym = 1;
+      g.status = p->status;
+      KF_TRY(gemm_bulk<B>(p, true, g));
+    }
+    if (P_full && t_full == t) KF_TRY((copy2d<double, B>(s, P_full, N, (const B*)p->tmpN, ldN, N, N)));
+  }
+  KF_CUDA_TRY(cudaMemcpyAsync(x_smooth, p->xs + N, (size_t)T * N * 8, cudaMemcpyDeviceToDevice, s));
+  return read_status(p, fail_step);
+}
+
+kf_status copy_inputs(kf_plan_s* p, const double* F, const int64_t* rp, const int64_t* col, const double* Q,
+                      const double* H, const double* R) {
+  cudaStream_t s = p->s;
+  const int64_t N = p->N, m = p->m;
+  if (p->d.f_kind == KF_F_CSR) {
+    KF_CUDA_TRY(cudaMemcpyAsync(p->F, F, p->d.f_nnz * 8, cudaMemcpyDeviceToDevice, s));
+    KF_CUDA_TRY(cudaMemcpyAsync(p->Frp, rp, (N + 1) * 8, cudaMemcpyDeviceToDevice, s));
+    KF_CUDA_TRY(cudaMemcpyAsync(p->Fcol, col, p->d.f_nnz * 8, cudaMemcpyDeviceToDevice, s));
+  } else if (p->d.f_kind == KF_F_DENSE) {
+    KF_CUDA_TRY(cudaMemcpyAsync(p->F, F, (size_t)N * N * 8, cudaMemcpyDeviceToDevice, s));
+    if (p->b == 8)
+      KF_TRY((copy2d<double, double>(s, (double*)p->Fb, p->ldN, F, N, N, N)));
+    else
+      KF_TRY((copy2d<float, double>(s, (float*)p->Fb, p->ldN, F, N, N, N)));
+  }
+  KF_CUDA_TRY(cudaMemcpyAsync(p->Q, Q, cov_count(p->d.q_kind, N) * 8, cudaMemcpyDeviceToDevice, s));
+  KF_CUDA_TRY(cudaMemcpyAsync(p->H, H, (size_t)m * N * 8, cudaMemcpyDeviceToDevice, s));
+  KF_CUDA_TRY(cudaMemcpyAsync(p->R, R, cov_count(p->d.r_kind, m) * 8, cudaMemcpyDeviceToDevice, s));
+  if (p->b == 8)
+    KF_TRY((copy2d<double, double>(s, (double*)p->Hb, p->ldN, H, N, m, N, true)));
+  else
+    KF_TRY((copy2d<float, double>(s, (float*)p->Hb, p->ldN, H, N, m, N, true)));
+  return KF_OK;
+}
+
+}  // namespace
+
+// =================================================================== C ABI
+
+extern "C" {
+
+kf_status kf_plan_footprint(const kf_desc* d, uint64_t* workspace_bytes, uint64_t* store_bytes,
+                            int32_t* checkpoint_every) {
+  KF_TRY(validate(d));
+  Sizes z = sizes_for(d);
+  int64_t c = 1;
+  uint64_t sbytes = 0;
+  kf_status st = choose_checkpoint(d, z, &c, &sbytes);
+  if (workspace_bytes) *workspace_bytes = z.workspace;
+  if (store_bytes) *store_bytes = sbytes;
+  if (checkpoint_every) *checkpoint_every = (int32_t)c;
+  return st;
+}
+
+kf_status kf_plan(kf_plan_t* out, const kf_desc* d) {
+  if (!out) return KF_ERR_ARG;
+  KF_TRY(validate(d));
+  if (d->prec == KF_PREC_MIXED_BF16X3 && !tc_available()) return KF_ERR_UNSUPPORTED;
+  Sizes z = sizes_for(d);
+  int64_t c = 1;
+  uint64_t store_bytes = 0;
+  KF_TRY(choose_checkpoint(d, z, &c, &store_bytes));
+
+  kf_plan_s* p = new kf_plan_s();
+  p->d = *d;
+  p->s = (cudaStream_t)d->stream;
+  p->N = d->N; p->m = d->m; p->T = d->T;
+  p->ldN = z.ldN; p->ldm = z.ldm;
+  p->b = z.b; p->sb = z.sb;
+  p->bulk = d->prec == KF_PREC_FP64 ? BULK_F64 : d->prec == KF_PREC_FP32 ? BULK_F32 : BULK_BF16X3;
+  p->solve = z.sb == 8 ? 0 : 1;
+  p->slot = z.slot;
+  p->ckpt = c;
+  p->launches0 = g_launches;
+  const int64_t N = p->N, m = p->m, T = p->T, ldN = p->ldN, ldm = p->ldm;
+  const size_t b = p->b, sb = p->sb;
+  kf_status st = KF_OK;
+  auto A = [&](auto** ptr, size_t bytes) {
+    if (st == KF_OK) st = dalloc(p, ptr, bytes);
+  };
+  A(&p->store, store_bytes - (c > 1 ? (size_t)(c - 1) * p->slot : 0));
+  if (c > 1) A(&p->seg, (size_t)(c - 1) * p->slot);
+  p->nck = c > 1 ? T / c + 1 : T + 1;
+  A(&p->xpred, (T + 1) * N * 8);
+  A(&p->xfilt, (T + 1) * N * 8);
+  A(&p->xs, (T + 1) * N * 8);
+  A(&p->nu, m * 8);
+  A(&p->dx, N * 8);
+  A(&p->P, p->slot);
+  A(&p->tmpN, p->slot);
+  A(&p->Ut, N * ldm * b);
+  A(&p->KV, N * 2 * ldm * b);
+  A(&p->VK, N * 2 * ldm * b);
+  A(&p->Hb, m * ldN * b);
+  A(&p->S, m * m * 8);
+  A(&p->S0, m * m * 8);
+  A(&p->Sdinv, round_up(m, 64) * 64 * 8);
+  A(&p->partials, kSplitsS * m * m * 8);
+  A(&p->Sl, m * m * b);
+  A(&p->Sldinv, round_up(m, 64) * 64 * b);
+  A(&p->S0b, m * m * b);
+  const int64_t nbs = sb == 8 ? 64 : 128;
+  A(&p->Lb, N * ldN * sb);
+  A(&p->Jb, N * ldN * sb);
+  A(&p->Ldinv, round_up(N, nbs) * nbs * sb);
+  if (sb != b) A(&p->Jm, p->slot);
+  A(&p->Wb, p->slot);
+  A(&p->Db, p->slot);
+  A(&p->Pn, p->slot);
+  if (d->f_kind == KF_F_CSR) {
+    A(&p->F, d->f_nnz * 8);
+    A(&p->Fcol, d->f_nnz * 8);
+    A(&p->Frp, (N + 1) * 8);
+  } else if (d->f_kind == KF_F_DENSE) {
+    A(&p->F, N * N * 8);
+    A(&p->Fb, p->slot);
+  }
+  A(&p->Q, cov_count(d->q_kind, N) * 8);
+  A(&p->H, m * N * 8);
+  A(&p->R, cov_count(d->r_kind, m) * 8);
+  A(&p->status, ST_WORDS * sizeof(int));
+  if (st == KF_OK && p->bulk == BULK_BF16X3) st = tc_scratch_alloc(p->tc, N, ldN, [&](void** ptr, size_t bytes) {
+    return dalloc(p, (char**)ptr, bytes);
+  });
+  if (st == KF_OK && cudaMallocHost(&p->status_h, ST_WORDS * sizeof(int)) != cudaSuccess) st = KF_ERR_CUDA;
+  if (st == KF_OK && cudaStreamSynchronize(p->s) != cudaSuccess) st = KF_ERR_CUDA;
+  if (st != KF_OK) {
+    kf_plan_destroy(p);
+    return st;
+  }
+  *out = p;
+  return KF_OK;
+}
+
+kf_status kf_filter(kf_plan_t p, const double* F, const int64_t* F_rowptr, const int64_t* F_col,
+                    const double* Q, const double* H, const double* R, const double* Y, const double* x0,
+                    const double* P0, double* x_filt, double* diagP_filt, int64_t* fail_step) {
+  if (fail_step) *fail_step = 0;
+  if (!p || !Q || !H || !R || !Y || !x0 || !P0 || !x_filt) return KF_ERR_ARG;
+  if (p->d.f_kind != KF_F_IDENTITY && !F) return KF_ERR_ARG;
+  if (p->d.f_kind == KF_F_CSR && (!F_rowptr || !F_col)) return KF_ERR_ARG;
+  p->filtered = false;
+  KF_TRY(copy_inputs(p, F, F_rowptr, F_col, Q, H, R));
+  kf_status st = p->b == 8 ? run_filter<double>(p, Y, x0, P0, x_filt, diagP_filt, fail_step)
+                           : run_filter<float>(p, Y, x0, P0, x_filt, diagP_filt, fail_step);
+  p->filtered = st == KF_OK;
+  return st;
+}
+
+kf_status fis_smooth(kf_plan_t p, double* x_smooth, double* diagP_smooth, double* P_smooth_at, int64_t t_full,
+                     int64_t* fail_step) {
+  if (fail_step) *fail_step = 0;
+  if (!p || !x_smooth) return KF_ERR_ARG;
+  if (P_smooth_at && (t_full < 1 || t_full > p->T)) return KF_ERR_ARG;
+  if (!p->filtered) return KF_ERR_STATE;
+  if (p->b == 8) return run_smoother<double, double>(p, x_smooth, diagP_smooth, P_smooth_at, t_full, fail_step);
+  if (p->sb == 8) return run_smoother<float, double>(p, x_smooth, diagP_smooth, P_smooth_at, t_full, fail_step);
+  return run_smoother<float, float>(p, x_smooth, diagP_smooth, P_smooth_at, t_full, fail_step);
+}
+
+kf_status kf_solve_host(kf_plan_t p, const double* F, const int64_t* F_rowptr, const int64_t* F_col,
+                        const double* Q, const double* H, const double* R, const double* Y, const double* x0,
+                        const double* P0, double* x_filt, double* diagP_filt, double* x_smooth,
+                        double* diagP_smooth, int64_t* fail_step) {
+  if (!p || !Q || !H || !R || !Y || !x0 || !P0) return KF_ERR_ARG;
+  const int64_t N = p->N, m = p->m, T = p->T;
+  cudaStream_t s = p->s;
+  kf_status st = KF_OK;
+  auto A = [&](auto** ptr, size_t bytes) {
+    if (st == KF_OK && *ptr == nullptr) st = dalloc(p, ptr, bytes);
+  };
+  A(&p->hY, T * m * 8);
+  A(&p->hx0, N * 8);
+  A(&p->hP0, N * N * 8);
+  A(&p->hQ, cov_count(p->d.q_kind, N) * 8);
+  A(&p->hH, m * N * 8);
+  A(&p->hR, cov_count(p->d.r_kind, m) * 8);
+  A(&p->hxf, T * N * 8);
+  A(&p->hdf, T * N * 8);
+  A(&p->hxs, T * N * 8);
+  A(&p->hds, T * N * 8);
+  if (p->d.f_kind == KF_F_CSR) {
+    A(&p->hF, p->d.f_nnz * 8);
+    A(&p->hFcol, p->d.f_nnz * 8);
+    A(&p->hFrp, (N + 1) * 8);
+  } else if (p->d.f_kind == KF_F_DENSE) {
+    A(&p->hF, N * N * 8);
+  }
+  KF_TRY(st);
+  auto H2D = [&](void* dst, const void* src, size_t bytes) {
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s);
+  };
+  KF_CUDA_TRY(H2D(p->hY, Y, T * m * 8));
+  KF_CUDA_TRY(H2D(p->hx0, x0, N * 8));
+  KF_CUDA_TRY(H2D(p->hP0, P0, N * N * 8));
+  KF_CUDA_TRY(H2D(p->hQ, Q, cov_count(p->d.q_kind, N) * 8));
+  KF_CUDA_TRY(H2D(p->hH, H, m * N * 8));
+  KF_CUDA_TRY(H2D(p->hR, R, cov_count(p->d.r_kind, m) * 8));
+  if (p->d.f_kind == KF_F_CSR) {
+    if (!F || !F_rowptr || !F_col) return KF_ERR_ARG;
+    KF_CUDA_TRY(H2D(p->hF, F, p->d.f_nnz * 8));
+    KF_CUDA_TRY(H2D(p->hFcol, F_col, p->d.f_nnz * 8));
+    KF_CUDA_TRY(H2D(p->hFrp, F_rowptr, (N + 1) * 8));
+  } else if (p->d.f_kind == KF_F_DENSE) {
+    if (!F) return KF_ERR_ARG;
+    KF_CUDA_TRY(H2D(p->hF, F, N * N * 8));
+  }
+  KF_TRY(kf_filter(p, p->hF, p->hFrp, p->hFcol, p->hQ, p->hH, p->hR, p->hY, p->hx0, p->hP0, p->hxf, p->hdf,
+                   fail_step));
+  KF_TRY(fis_smooth(p, p->hxs, p->hds, nullptr, -1, fail_step));
+  auto D2H = [&](void* dst, const void* src, size_t bytes) {
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s);
+  };
+  if (x_filt) KF_CUDA_TRY(D2H(x_filt, p->hxf, T * N * 8));
+  if (diagP_filt) KF_CUDA_TRY(D2H(diagP_filt, p->hdf, T * N * 8));
+  if (x_smooth) KF_CUDA_TRY(D2H(x_smooth, p->hxs, T * N * 8));
+  if (diagP_smooth) KF_CUDA_TRY(D2H(diagP_smooth, p->hds, T * N * 8));
+  KF_CUDA_TRY(cudaStreamSynchronize(s));
+  return KF_OK;
+}
+
+kf_status kf_plan_profile(kf_plan_t p, int32_t enable) {
+  if (!p) return KF_ERR_ARG;
+  KF_CUDA_TRY(cudaStreamSynchronize(p->s));
+  for (auto& mk : p->marks) {
+    p->pool.push_back(mk.a);
+    p->pool.push_back(mk.b);
+  }
+  p->marks.clear();
+  p->prof = enable != 0;
+  return KF_OK;
+}
+
+kf_status kf_plan_profile_read(kf_plan_t p, int32_t cls, int64_t* launches, double* total_ms) {
+  if (!p || cls < 0 || cls >= KF_KC_COUNT) return KF_ERR_ARG;
+  KF_CUDA_TRY(cudaStreamSynchronize(p->s));
+  int64_t n = 0;
+  double ms = 0.0;
+  for (auto& mk : p->marks) {
+    if (mk.cls != cls) continue;
+    float f = 0.f;
+    KF_CUDA_TRY(cudaEventElapsedTime(&f, mk.a, mk.b));
+    ms += f;
+    ++n;
+  }
+  if (launches) *launches = n;
+  if (total_ms) *total_ms = ms;
+  return KF_OK;
+}
+
+int64_t kf_plan_launch_count(kf_plan_t p) { return p ? g_launches - p->launches0 : 0; }
+
+void kf_plan_destroy(kf_plan_t p) {
+  if (!p) return;
+  if (p->s) cudaStreamSynchronize(p->s);
+  for (void* a : p->allocs) cudaFree(a);
+  for (auto& mk : p->marks) {
+    cudaEventDestroy(mk.a);
+    cudaEventDestroy(mk.b);
+  }
+  for (auto e : p->pool) cudaEventDestroy(e);
+  if (p->status_h) cudaFreeHost(p->status_h);
+  delete p;
+}
+
+const char* kf_strerror(kf_status s) {
+  switch (s) {
+    case KF_OK: return "ok";
+    case KF_ERR_ARG: return "invalid argument";
+    case KF_ERR_NOT_PD: return "matrix not positive definite";
+    case KF_ERR_BUDGET: return "covariance store does not fit the memory budget";
+    case KF_ERR_CUDA: return "CUDA runtime error";
+    case KF_ERR_NUMERIC: return "non-finite value or non-positive variance";
+    case KF_ERR_TIMEOUT: return "bounded device wait expired";
+    case KF_ERR_STATE: return "call order violated (fis_smooth needs a successful kf_filter)";
+    case KF_ERR_UNSUPPORTED: return "unsupported in this build";
+  }
+  return "unknown status";
+}
+
+}  // extern "C"

@@ -1,0 +1,270 @@
+// Bandwidth-bound helper kernels: copies/conversions, covariance additions,
+// matrix-vector products for the means (eqns 6, 10, 12), the innovation and
+// its covariance S = H P H^T + R (eqn 8), the bf16 hi/lo split, diagonals.
+#include "ops.cuh"
+
+namespace kfm {
+
+__device__ __forceinline__ double cov_value(int kind, const double* q, int64_t n, int64_t i, int64_t j) {
+  if (kind == 0) return i == j ? q[0] : 0.0;
+  if (kind == 1) return i == j ? q[i] : 0.0;
+  if (kind == 2) return q[i * n + j];
+  return 0.0;
+}
+
+template <typename Tdst, typename Tsrc>
+__global__ void copy2d_kernel(Tdst* dst, int64_t ldd, const Tsrc* src, int64_t lds, int64_t rows,
+                              int64_t cols, int64_t pad_to) {
+  for (int64_t i = blockIdx.y; i < rows; i += gridDim.y)
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < pad_to;
+         j += (int64_t)gridDim.x * blockDim.x)
+      dst[i * ldd + j] = j < cols ? (Tdst)src[i * lds + j] : (Tdst)0;
+}
+
+template <typename Tdst, typename Tsrc>
+kf_status copy2d(cudaStream_t s, Tdst* dst, int64_t ldd, const Tsrc* src, int64_t lds, int64_t rows,
+                 int64_t cols, bool zero_pad) {
+  if (rows <= 0 || cols <= 0) return KF_OK;
+  int64_t pad_to = zero_pad ? ldd : cols;
+  dim3 grid((unsigned)std::min<int64_t>(ceil_div(pad_to, 256), 64), (unsigned)std::min<int64_t>(rows, 65535));
+  copy2d_kernel<Tdst, Tsrc><<<grid, 256, 0, s>>>(dst, ldd, src, lds, rows, cols, pad_to);
+  ++g_launches;
+  return launch_check("copy2d");
+}
+
+template <typename Tdst, typename Tsrc>
+__global__ void add_cov_kernel(Tdst* dst, int64_t ldd, const Tsrc* src, int64_t lds, int64_t n, int kind,
+                               const double* q) {
+  for (int64_t i = blockIdx.y; i < n; i += gridDim.y)
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+      dst[i * ldd + j] = (Tdst)((double)src[i * lds + j] + cov_value(kind, q, n, i, j));
+}
+
+template <typename Tdst, typename Tsrc>
+kf_status add_cov(cudaStream_t s, Tdst* dst, int64_t ldd, const Tsrc* src, int64_t lds, int64_t n,
+                  int q_kind, const double* q) {
+  if (n <= 0) return KF_OK;
+  dim3 grid((unsigned)std::min<int64_t>(ceil_div(n, 256), 64), (unsigned)std::min<int64_t>(n, 65535));
+  add_cov_kernel<Tdst, Tsrc><<<grid, 256, 0, s>>>(dst, ldd, src, lds, n, q_kind, q);
+  ++g_launches;
+  return launch_check("add_cov");
+}
+
+// one warp per row, float64 accumulation
+template <typename T>
+__global__ void gemv_kernel(int64_t rows, int64_t cols, const T* A, int64_t lda, const double* x,
+                            const double* ybase, double sign, double* y) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = warp; i < rows; i += nwarps) {
+    double acc = 0.0;
+    for (int64_t j = lane; j < cols; j += 32) acc = fma((double)A[i * lda + j], x[j], acc);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) y[i] = ybase ? ybase[i] + sign * acc : acc;
+  }
+}
+
+template <typename T>
+kf_status gemv(cudaStream_t s, int64_t rows, int64_t cols, const T* A, int64_t lda, const double* x,
+               const double* ybase, double sign, double* y) {
+  if (rows <= 0) return KF_OK;
+  unsigned blocks = (unsigned)std::min<int64_t>(ceil_div(rows * 32, 256), 4096);
+  gemv_kernel<T><<<blocks, 256, 0, s>>>(rows, cols, A, lda, x, ybase, sign, y);
+  ++g_launches;
+  return launch_check("gemv");
+}
+
+__global__ void vsub_kernel(int64_t n, const double* a, const double* b, double* d) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    d[i] = a[i] - b[i];
+}
+
+kf_status vsub(cudaStream_t s, int64_t n, const double* a, const double* b, double* d) {
+  if (n <= 0) return KF_OK;
+  vsub_kernel<<<(unsigned)std::min<int64_t>(ceil_div(n, 256), 1024), 256, 0, s>>>(n, a, b, d);
+  ++g_launches;
+  return launch_check("vsub");
+}
+
+__global__ void innovation_kernel(int64_t m, int64_t N, const double* H, const double* x, const double* y,
+                                  double* nu, int* status, int step) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = warp; i < m; i += nwarps) {
+    double acc = 0.0;
+    for (int64_t j = lane; j < N; j += 32) acc = fma(H[i * N + j], x[j], acc);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+      double v = y[i] - acc;
+      nu[i] = v;
+      if (!isfinite(v)) status_set(status, KF_ERR_NUMERIC, step, (int)i);
+    }
+  }
+}
+
+kf_status innovation(cudaStream_t s, int64_t m, int64_t N, const double* H, const double* x,
+                     const double* y, double* nu, int* status, int step) {
+  unsigned blocks = (unsigned)std::min<int64_t>(ceil_div(m * 32, 256), 1024);
+  innovation_kernel<<<blocks, 256, 0, s>>>(m, N, H, x, y, nu, status, step);
+  ++g_launches;
+  return launch_check("innovation");
+}
+
+// partials[split][i][j] = sum_{k in chunk} H[i,k] Ut[k,j]; 32 x 32 output tile per CTA.
+// float32 operands are multiplied in float32 over 32-long runs and summed in float64.
+template <typename T>
+__global__ void __launch_bounds__(256) innov_cov_partial_kernel(int m, int N, const double* H, int64_t ldh,
+                                                                const T* Ut, int64_t ldu, double* partials,
+                                                                int chunk) {
+  __shared__ T Hs[32][33];
+  __shared__ T Us[32][33];
+  const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+  const int split = blockIdx.z;
+  const int k_begin = split * chunk;
+  const int k_end = min(N, k_begin + chunk);
+  const int tid = threadIdx.x;
+  const int tx = tid % 32, ty = tid / 32;  // ty: 0..7, each thread 4 rows (ty + 8 r)
+  double acc[4] = {0, 0, 0, 0};
+  for (int k0 = k_begin; k0 < k_end; k0 += 32) {
+    for (int l = tid; l < 32 * 32; l += 256) {
+      int r = l / 32, c = l % 32;
+      int gi = i0 + r, gk = k0 + c;
+      Hs[r][c] = (gi < m && gk < k_end) ? (T)H[(int64_t)gi * ldh + gk] : T(0);
+      int gk2 = k0 + r, gj = j0 + c;
+      Us[r][c] = (gk2 < k_end && gj < m) ? Ut[(int64_t)gk2 * ldu + gj] : T(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      T a = T(0);
+#pragma unroll 8
+      for (int kk = 0; kk < 32; ++kk) a = fma(Hs[ty + 8 * r][kk], Us[kk][tx], a);
+      acc[r] += (double)a;
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    int gi = i0 + ty + 8 * r, gj = j0 + tx;
+    if (gi < m && gj < m) partials[((int64_t)split * m + gi) * m + gj] = acc[r];
+  }
+}
+
+// S = sym(sum_split partials) + R
+__global__ void innov_cov_reduce_kernel(int m, const double* partials, int splits, int r_kind,
+                                        const double* R, double* S, int64_t lds) {
+  int64_t total = (int64_t)m * m;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    int i = (int)(idx / m), j = (int)(idx % m);
+    if (j > i) continue;
+    double a = 0.0, b = 0.0;
+    for (int sp = 0; sp < splits; ++sp) {
+      a += partials[((int64_t)sp * m + i) * m + j];
+      b += partials[((int64_t)sp * m + j) * m + i];
+    }
+    double v = 0.5 * (a + b) + cov_value(r_kind, R, m, i, j);
+    S[(int64_t)i * lds + j] = v;
+    S[(int64_t)j * lds + i] = v;
+  }
+}
+
+template <typename T>
+kf_status innovation_cov(cudaStream_t s, int m, int N, const double* H, int64_t ldh, const T* Ut,
+                         int64_t ldu, int r_kind, const double* R, double* S, int64_t lds,
+                         double* partials, int splits) {
+  int chunk = (int)round_up(ceil_div(N, splits), 32);
+  int used = (int)ceil_div(N, chunk);
+  dim3 grid((unsigned)ceil_div(m, 32), (unsigned)ceil_div(m, 32), (unsigned)used);
+  innov_cov_partial_kernel<T><<<grid, 256, 0, s>>>(m, N, H, ldh, Ut, ldu, partials, chunk);
+  ++g_launches;
+  KF_TRY(launch_check("innov_cov_partial"));
+  unsigned blocks = (unsigned)std::min<int64_t>(ceil_div((int64_t)m * m, 256), 1024);
+  innov_cov_reduce_kernel<<<blocks, 256, 0, s>>>(m, partials, used, r_kind, R, S, lds);
+  ++g_launches;
+  return launch_check("innov_cov_reduce");
+}
+
+__global__ void spmv_kernel(int64_t N, const int64_t* rowptr, const int64_t* col, const double* val,
+                            const double* x, double* y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) acc = fma(val[k], x[col[k]], acc);
+    y[i] = acc;
+  }
+}
+
+kf_status predict_mean(cudaStream_t s, int f_kind, int64_t N, const double* F, const int64_t* rowptr,
+                       const int64_t* col, const double* x, double* x_out) {
+  if (f_kind == KF_F_IDENTITY) {
+    KF_CUDA_TRY(cudaMemcpyAsync(x_out, x, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    return KF_OK;
+  }
+  if (f_kind == KF_F_CSR) {
+    spmv_kernel<<<(unsigned)std::min<int64_t>(ceil_div(N, 256), 1024), 256, 0, s>>>(N, rowptr, col, F, x, x_out);
+    ++g_launches;
+    return launch_check("spmv");
+  }
+  return gemv<double>(s, N, N, F, N, x, nullptr, 1.0, x_out);
+}
+
+__global__ void split_bf16_kernel(int64_t rows, int64_t cols, const float* A, int64_t lda, __nv_bfloat16* hi,
+                                  __nv_bfloat16* lo, int64_t ldh) {
+  for (int64_t i = blockIdx.y; i < rows; i += gridDim.y)
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < ldh; j += (int64_t)gridDim.x * blockDim.x) {
+      float a = j < cols ? A[i * lda + j] : 0.0f;
+      __nv_bfloat16 h = __float2bfloat16_rn(a);
+      __nv_bfloat16 l = __float2bfloat16_rn(a - __bfloat162float(h));
+      hi[i * ldh + j] = h;
+      lo[i * ldh + j] = l;
+    }
+}
+
+kf_status split_bf16(cudaStream_t s, int64_t rows, int64_t cols, const float* A, int64_t lda,
+                     __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t ldh) {
+  if (rows <= 0) return KF_OK;
+  dim3 grid((unsigned)std::min<int64_t>(ceil_div(ldh, 256), 64), (unsigned)std::min<int64_t>(rows, 65535));
+  split_bf16_kernel<<<grid, 256, 0, s>>>(rows, cols, A, lda, hi, lo, ldh);
+  ++g_launches;
+  return launch_check("split_bf16");
+}
+
+template <typename T>
+__global__ void diag_kernel(int64_t n, const T* A, int64_t lda, double* d) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    d[i] = (double)A[i * lda + i];
+}
+
+template <typename T>
+kf_status diag_extract(cudaStream_t s, int64_t n, const T* A, int64_t lda, double* diag_out) {
+  if (n <= 0) return KF_OK;
+  diag_kernel<T><<<(unsigned)std::min<int64_t>(ceil_div(n, 256), 1024), 256, 0, s>>>(n, A, lda, diag_out);
+  ++g_launches;
+  return launch_check("diag");
+}
+
+#define KFM_INST2(D, S)                                                                             \
+  template kf_status copy2d<D, S>(cudaStream_t, D*, int64_t, const S*, int64_t, int64_t, int64_t, bool); \
+  template kf_status add_cov<D, S>(cudaStream_t, D*, int64_t, const S*, int64_t, int64_t, int, const double*);
+KFM_INST2(double, double)
+KFM_INST2(float, float)
+KFM_INST2(double, float)
+KFM_INST2(float, double)
+#undef KFM_INST2
+
+template kf_status gemv<double>(cudaStream_t, int64_t, int64_t, const double*, int64_t, const double*,
+                                const double*, double, double*);
+template kf_status gemv<float>(cudaStream_t, int64_t, int64_t, const float*, int64_t, const double*,
+                               const double*, double, double*);
+template kf_status innovation_cov<double>(cudaStream_t, int, int, const double*, int64_t, const double*,
+                                          int64_t, int, const double*, double*, int64_t, double*, int);
+template kf_status innovation_cov<float>(cudaStream_t, int, int, const double*, int64_t, const float*,
+                                         int64_t, int, const double*, double*, int64_t, double*, int);
+template kf_status diag_extract<double>(cudaStream_t, int64_t, const double*, int64_t, double*);
+template kf_status diag_extract<float>(cudaStream_t, int64_t, const float*, int64_t, double*);
+
+}  // namespace kfm

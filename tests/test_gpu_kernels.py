@@ -1,0 +1,145 @@
+"""Kernel-level GPU checks through the C ABI (include/kfmeg_kernels.h) against
+plain float64 references of the same operation, on ragged shapes that span
+several tiles and partial tails."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1107_4192_gb300 import binding as B  # noqa: E402
+from paper_1107_4192_gb300 import synth  # noqa: E402
+
+DT = {0: torch.float64, 1: torch.float32}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1107_4192_gb300 import build
+    build.build()
+    B.lib()
+
+
+def _dev(a, dt):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda", DT[dt])
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+@pytest.mark.parametrize("transB", [0, 1])
+@pytest.mark.parametrize("M,N,K", [(1, 1, 1), (7, 5, 3), (129, 65, 200), (300, 130, 77), (64, 64, 0)])
+def test_gemm(dtype, transB, M, N, K):
+    rng = np.random.default_rng(M * 1000 + N * 10 + K)
+    A = rng.standard_normal((M, K))
+    Bm = rng.standard_normal((N, K)) if transB else rng.standard_normal((K, N))
+    C0 = rng.standard_normal((M, N))
+    alpha, beta = -0.7, 1.3
+    ref = alpha * A @ (Bm.T if transB else Bm) + beta * C0
+    dA, dB, dC = _dev(A, dtype), _dev(Bm, dtype), _dev(C0, dtype)
+    B.kfx_gemm(dtype, transB, 0, M, N, K, alpha, dA, max(K, 1), dB, (K if transB else N) or 1, beta, dC, N)
+    got = dC.double().cpu().numpy()
+    tol = 1e-13 if dtype == 0 else 2e-5
+    assert np.linalg.norm(got - ref) <= tol * max(np.linalg.norm(ref), 1e-300) * max(1, np.sqrt(K) / 4)
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+@pytest.mark.parametrize("n,K", [(1, 3), (63, 64), (130, 20), (257, 129)])
+def test_gemm_symmetric_mirror(dtype, n, K):
+    rng = np.random.default_rng(n + K)
+    A = rng.standard_normal((n, K))
+    Bm = rng.standard_normal((n, K))
+    S0 = rng.standard_normal((n, n))
+    S0 = S0 + S0.T
+    ref = A @ Bm.T + S0
+    dC = _dev(S0, dtype)
+    B.kfx_gemm(dtype, 1, 1, n, n, K, 1.0, _dev(A, dtype), K, _dev(Bm, dtype), K, 1.0, dC, n)
+    got = dC.double().cpu().numpy()
+    assert np.array_equal(got, got.T), "mirror must give an exactly symmetric result"
+    low = np.tril(np.ones((n, n), bool))
+    tol = 1e-13 if dtype == 0 else 2e-5
+    assert np.abs(got - ref)[low].max() <= tol * np.abs(ref).max() * max(1, np.sqrt(K) / 4)
+
+
+def _spd(n, seed, cond=50.0):
+    rng = np.random.default_rng(seed)
+    Qm, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    ev = np.geomspace(1.0, cond, n)
+    return (Qm * ev) @ Qm.T
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+@pytest.mark.parametrize("n,M", [(1, 4), (5, 3), (64, 70), (65, 65), (129, 31), (300, 257)])
+def test_cholesky_and_right_solve(dtype, n, M):
+    A = _spd(n, n * 7 + M)
+    rng = np.random.default_rng(n)
+    Bm = rng.standard_normal((M, n))
+    dA, dB = _dev(A, dtype), _dev(Bm, dtype)
+    st, fi = B.kfx_posv_right(dtype, n, dA, n, M, dB, n)
+    assert st == 0 and fi == -1
+    L = np.tril(dA.double().cpu().numpy())
+    Lref = np.linalg.cholesky(A)
+    X = dB.double().cpu().numpy()
+    Xref = np.linalg.solve(A, Bm.T).T
+    if dtype == 0:
+        assert np.abs(L - Lref).max() <= 1e-13 * np.abs(Lref).max()
+        assert np.linalg.norm(X - Xref) <= 1e-11 * np.linalg.norm(Xref)
+    else:
+        assert np.abs(L - Lref).max() <= 1e-5 * np.abs(Lref).max()
+        assert np.linalg.norm(X - Xref) <= 1e-4 * np.linalg.norm(Xref)
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+def test_cholesky_reports_first_bad_pivot(dtype):
+    n = 150
+    A = _spd(n, 3)
+    A[97, :] = 0.0
+    A[:, 97] = 0.0  # pivot 97 becomes 0 (all earlier ones stay positive)
+    dA = _dev(A, dtype)
+    st, fi = B.kfx_posv_right(dtype, n, dA, n, 0, None, n)
+    assert st == B.KF_ERR_NOT_PD and fi == 97
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+@pytest.mark.parametrize("q_kind", [-1, 0, 1, 2])
+def test_spmm_fpft(dtype, q_kind):
+    N = 324
+    neigh = synth.hemisphere_mesh(N)
+    F = synth.mesh_coupling(neigh)
+    rng = np.random.default_rng(1)
+    Fd = np.zeros((N, N))
+    for i in range(N):
+        Fd[i, F.col[F.rowptr[i]:F.rowptr[i + 1]]] = F.val[F.rowptr[i]:F.rowptr[i + 1]]
+    Fd[Fd != 0] *= rng.uniform(0.5, 1.0, size=(Fd != 0).sum())  # non-symmetric values
+    vals = np.concatenate([Fd[i, F.col[F.rowptr[i]:F.rowptr[i + 1]]] for i in range(N)])
+    A = rng.standard_normal((N, N))
+    P = A @ A.T / N
+    Q = {-1: None, 0: np.array([0.3]), 1: rng.uniform(0.1, 1, N), 2: P * 0.1}[q_kind]
+    Qd = {-1: 0, 0: 0.3 * np.eye(N), 1: np.diag(Q) if q_kind == 1 else 0, 2: Q}[q_kind]
+    ref = Fd @ P @ Fd.T + Qd
+    ld = 384
+    Pp = np.zeros((N, ld))
+    Pp[:, :N] = P
+    out = torch.zeros(N, ld, dtype=DT[dtype], device="cuda")
+    tQ = None if Q is None else torch.from_numpy(np.ascontiguousarray(Q, np.float64)).cuda()
+    B.kfx_spmm_fpft(dtype, N, torch.from_numpy(F.rowptr).cuda(), torch.from_numpy(F.col).cuda(),
+                    torch.from_numpy(vals).cuda(), _dev(Pp, dtype), ld, out, ld, q_kind, tQ)
+    got = out.double().cpu().numpy()[:, :N]
+    tol = 1e-14 if dtype == 0 else 1e-6
+    assert np.abs(got - ref).max() <= tol * np.abs(ref).max()
+
+
+def test_split_bf16():
+    rng = np.random.default_rng(0)
+    rows, cols, ld = 37, 100, 128
+    A = rng.standard_normal((rows, cols)).astype(np.float32) * np.exp(rng.uniform(-5, 5, (rows, cols))).astype(np.float32)
+    dA = torch.from_numpy(A).cuda()
+    hi = torch.full((rows, ld), 7.0, dtype=torch.bfloat16, device="cuda")
+    lo = torch.full((rows, ld), 7.0, dtype=torch.bfloat16, device="cuda")
+    B.kfx_split_bf16(rows, cols, dA, cols, hi, lo, ld)
+    h = hi.float().cpu().numpy()
+    lw = lo.float().cpu().numpy()
+    assert np.array_equal(h[:, :cols], torch.from_numpy(A).bfloat16().float().numpy())
+    assert np.all(h[:, cols:] == 0) and np.all(lw[:, cols:] == 0)
+    rel = np.abs(h[:, :cols] + lw[:, :cols] - A) / np.abs(A)
+    assert rel.max() <= 2.0 ** -16
