@@ -1,0 +1,354 @@
+"""Throughput of the Kalman filter + fixed-interval smoother on one GB300.
+
+Workload: N = 8196 sources, m = 306 sensors, T = 300 time steps, random-walk
+dynamics (F = I), Q = 1e-2 I, R = diag U(0.5, 2), P0 = I, synthetic lead field
+and patch sources (seed 2).  One step = one whole epoch: the forward filter
+over all T steps and the backward smoother over T - 1 steps.  The metric is
+KF+FIS timesteps/s (T per epoch), with algorithmic TFLOP/s beside it.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+               [--prec mixed|fp32|fp64] [--solve fp32|fp64]
+
+Multi-GPU (torchrun): every rank runs its own independent epoch (replicas;
+the recursion in t is sequential and the epochs share nothing), the timed
+region is bracketed by a barrier and device synchronisation, and the
+slowest rank's time is used.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "KF+FIS timesteps/s & TFLOP/s at N=8196,m=306 vs FP64 plain; serve p50/p99"
+N_SRC, M_SENS, T_STEPS = 8196, 306, 300
+
+
+def flops_per_timestep(N, m):
+    """Algorithmic flops of one filter step plus one smoother step.
+
+    filter:   U^T = P H^T (2mN^2), S = H U^T (2m^2N), Cholesky of S (m^3/3),
+              K = U^T S^{-1} (2m^2N), P - K U (2mN^2)
+    smoother: Cholesky of P_{t+1|t} (N^3/3), two triangular solves with N
+              right-hand sides (2N^3), W = J D (2N^3), P + W J^T on the lower
+              triangle (N^2 (N+1)), mean (2N^2)
+    """
+    filt = 4 * m * N * N + 4 * m * m * N + m ** 3 / 3
+    smooth = N ** 3 / 3 + 2 * N ** 3 + 2 * N ** 3 + N * N * (N + 1) + 2 * N * N
+    return filt + smooth, smooth, filt
+
+
+def smoother_gemm_flops_per_launch(N):
+    """Average algorithmic flops of one smoother product launch (W = J D, then W J^T lower)."""
+    return (2 * N ** 3 + N * N * (N + 1)) / 2
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
+        "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.file = None
+
+    def __enter__(self):
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"], stdout=self.file,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        self.file.flush()
+
+    def summary(self):
+        rows = []
+        try:
+            with open(self.file.name) as f:
+                for line in f:
+                    parts = [x.strip() for x in line.split(",")]
+                    if len(parts) >= 9:
+                        rows.append(parts)
+        finally:
+            os.unlink(self.file.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        power = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(power) if power else None}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="mixed", choices=["mixed", "fp32", "fp64"])
+    ap.add_argument("--solve", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--T", type=int, default=T_STEPS, help="time steps per epoch (the workload uses 300)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-plain", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_oracle_timestep(prob, T_sample=2):
+    """Times the CPU oracle as it stands: T_sample filter steps then one smoother step."""
+    from oracle import kf_oracle as ko
+    N = prob.N
+    F = np.eye(N)
+    Q = ko.dense_cov(prob.q_kind, prob.Q, N)
+    R = ko.dense_cov(prob.r_kind, prob.R, prob.m)
+    P0 = prob.p0_scale * np.eye(N)
+    t0 = time.perf_counter()
+    filt = ko.kalman_filter(F, Q, prob.H, R, prob.Y[:T_sample], prob.x0, P0)
+    t1 = time.perf_counter()
+    ko.rts_smoother(F, filt)
+    t2 = time.perf_counter()
+    per_step = (t1 - t0) / T_sample + (t2 - t1) / (T_sample - 1)
+    return per_step, f"{T_sample} filter steps + {T_sample - 1} smoother step of the N={N}, m={prob.m} workload " \
+                     f"(float64 numpy oracle); rate = 1 / (filter step + smoother step)"
+
+
+def host_threads():
+    try:
+        import threadpoolctl
+        info = threadpoolctl.threadpool_info()
+        n = max((i.get("num_threads", 0) for i in info), default=0)
+        if n:
+            return n
+    except Exception:
+        pass
+    return os.cpu_count() or 1
+
+
+def run_reference(args, world, rank):
+    """The oracle timed on the host cores, same workload and metric (rank 0 only)."""
+    if rank != 0:
+        return
+    from paper_1107_4192_gb300 import synth
+    prob = synth.config2(T=2)
+    for _ in range(args.warmup):
+        cpu_oracle_timestep(prob)
+    times = [cpu_oracle_timestep(prob)[0] for _ in range(args.steps)]
+    sample = (f"per step: 2 filter steps + 1 smoother step of the N={N_SRC}, m={M_SENS} workload (float64 numpy "
+              f"oracle); rate = 1 / (filter step + smoother step)")
+    per = float(np.mean(times))
+    value = 1.0 / per
+    line = {"metric": METRIC, "value": value, "unit": "timesteps/s", "n_gpus": 0, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": prob.name.replace("T2", f"T{T_STEPS}"), "N": N_SRC, "m": M_SENS, "T": T_STEPS},
+            "cpu_baseline": {"value": value, "unit": "timesteps/s", "cores": host_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "timesteps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    import torch
+    import torch.distributed as dist
+
+    from paper_1107_4192_gb300 import binding as B
+    from paper_1107_4192_gb300 import build, solver, synth
+
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    build.build()
+    B.lib()
+    prec = {"mixed": B.KF_PREC_MIXED_BF16X3, "fp32": B.KF_PREC_FP32, "fp64": B.KF_PREC_FP64}[args.prec]
+    solve = {"fp32": B.KF_SOLVE_FP32, "fp64": B.KF_SOLVE_FP64}[args.solve]
+    T = args.T
+    prob = synth.config2(T=T)
+    d = solver.upload(prob)
+    stream = torch.cuda.current_stream()
+    plan = solver.Plan.for_inputs(d, prob.N, prob.m, T, prec=prec, solve_prec=solve,
+                                  joseph_every=16 if args.prec == "mixed" else 0, stream=stream.cuda_stream)
+    outs = {k: torch.empty(T, prob.N, dtype=torch.float64, device="cuda") for k in ("xf", "df", "xs", "ds")}
+
+    def epoch():
+        B.kf_filter(plan.handle, d.F, d.F_rowptr, d.F_col, d.Q, d.H, d.R, d.Y, d.x0, d.P0, outs["xf"], outs["df"])
+        B.fis_smooth(plan.handle, outs["xs"], outs["ds"])
+
+    for _ in range(args.warmup):
+        epoch()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    B.kf_plan_profile(plan.handle, True)
+    launches0 = B.kf_plan_launch_count(plan.handle)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            epoch()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    launches = B.kf_plan_launch_count(plan.handle) - launches0
+    prof = {c: B.kf_plan_profile_read(plan.handle, c) for c in range(5)}
+    B.kf_plan_profile(plan.handle, False)
+    if world > 1:
+        t = torch.tensor([elapsed], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    clocks = clk.summary()
+
+    # end to end through the host-buffer entry point (inputs from pinned host memory, outputs back)
+    h = solver.host_inputs(prob)
+    pin = lambda a: None if a is None else torch.from_numpy(a).pin_memory()
+    hin = {k: pin(h[k]) for k in ("F", "F_rowptr", "F_col", "Q", "H", "R", "Y", "x0", "P0")}
+    hout = {k: torch.empty(T, prob.N, dtype=torch.float64).pin_memory() for k in ("xf", "df", "xs", "ds")}
+    h2d = sum(v.numel() * v.element_size() for v in hin.values() if v is not None)
+    d2h = sum(v.numel() * v.element_size() for v in hout.values())
+    e2e_steps = max(1, args.e2e_steps)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        B.kf_solve_host(plan.handle, hin["F"], hin["F_rowptr"], hin["F_col"], hin["Q"], hin["H"], hin["R"], hin["Y"],
+                        hin["x0"], hin["P0"], hout["xf"], hout["df"], hout["xs"], hout["ds"])
+    e2e_time = (time.perf_counter() - t0) / e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_time], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_time = float(t.item())
+    plan.close()
+
+    N, m = prob.N, prob.m
+    total_f, smooth_f, filt_f = flops_per_timestep(N, m)
+    value = world * args.steps * T / elapsed
+    ms_per_step = elapsed / args.steps * 1e3
+    peaks, peak_src = load_peaks()
+
+    # dominant kernel class by device time inside the timed region
+    names = {0: "filter_update", 1: "innovation", 2: "smoother_gemm", 3: "smoother_solve", 4: "predict"}
+    dom = max(prof, key=lambda c: prof[c][1])
+    n_l, ms_l = prof[dom]
+    avg_s = ms_l / 1e3 / max(n_l, 1)
+    if dom == 2:
+        work = smoother_gemm_flops_per_launch(N)
+        if args.prec == "mixed":
+            roof = {"bound": "tensor", "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s"}
+        else:
+            roof = {"bound": "alu", "peak": 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12 /
+                    (1 if args.prec == "fp32" else 64), "unit": "TFLOP/s"}
+        achieved = work / avg_s / 1e12
+    elif dom == 3:
+        work = (N ** 3 / 3 + 2 * N ** 3)
+        per_elt_peak = 1.25 if args.solve == "fp64" or args.prec == "fp64" else \
+            152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        roof = {"bound": "alu", "peak": per_elt_peak, "unit": "TFLOP/s"}
+        achieved = work / avg_s / 1e12
+    else:
+        byt = {0: 3.0, 1: 1.0, 4: 2.0}[dom] * N * N * (8 if args.prec == "fp64" else 4)
+        roof = {"bound": "hbm", "peak": peaks["hbm_gbs"], "unit": "GB/s"}
+        achieved = byt / avg_s / 1e9
+    roof.update({"kernel": names[dom], "achieved": achieved, "frac": achieved / roof["peak"], "traffic": None,
+                 "peak_source": peak_src, "launches": n_l, "avg_launch_ms": avg_s * 1e3})
+
+    line = {"metric": METRIC, "value": value, "unit": "timesteps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": {"mixed": "bf16x3+f32", "fp32": "f32", "fp64": "f64"}[args.prec] +
+                     ("" if args.prec == "fp64" else f"/solve-{args.solve}"),
+            "data": "synthetic",
+            "config": {"workload": prob.name, "N": N, "m": m, "T": T, "F": "identity", "precision": args.prec,
+                       "solve": args.solve if args.prec != "fp64" else "fp64",
+                       "joseph_every": 16 if args.prec == "mixed" else 0,
+                       "parallelism": f"replicas{world}",
+                       "l2": "working set > L2 (covariance store of T N x N matrices)"},
+            "tflops": value * total_f / 1e12,
+            "roofline": roof,
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "e2e": {"value": world * T / e2e_time, "unit": "timesteps/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "phase_ms": {names[c]: prof[c][1] / args.steps for c in prof}}
+
+    if rank == 0 and world == 1 and not args.no_fp64_plain and args.prec != "fp64":
+        line["fp64_plain"] = fp64_plain_prefix(prob, B, solver, synth, torch)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        per, sample = cpu_oracle_timestep(synth.config2(T=2))
+        line["cpu_baseline"] = {"value": 1.0 / per, "unit": "timesteps/s", "cores": host_threads(), "kind": "oracle",
+                                "sample": sample}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def fp64_plain_prefix(prob, B, solver, synth, torch, T_pre=3):
+    """Plain float64 path on the first T_pre steps of the same workload (a full
+    float64 epoch takes minutes); rate = 1 / (filter step + smoother step)."""
+    p = synth.config2(T=T_pre)
+    d = solver.upload(p)
+    plan = solver.Plan.for_inputs(d, p.N, p.m, T_pre, prec=B.KF_PREC_FP64,
+                                  stream=torch.cuda.current_stream().cuda_stream)
+    x = torch.empty(T_pre, p.N, dtype=torch.float64, device="cuda")
+    B.kf_filter(plan.handle, d.F, d.F_rowptr, d.F_col, d.Q, d.H, d.R, d.Y, d.x0, d.P0, x)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    B.kf_filter(plan.handle, d.F, d.F_rowptr, d.F_col, d.Q, d.H, d.R, d.Y, d.x0, d.P0, x)
+    t1 = time.perf_counter()
+    B.fis_smooth(plan.handle, x)
+    t2 = time.perf_counter()
+    plan.close()
+    per = (t1 - t0) / T_pre + (t2 - t1) / (T_pre - 1)
+    return {"value": 1.0 / per, "unit": "timesteps/s", "sample": f"T={T_pre} prefix, float64 throughout",
+            "filter_ms_per_step": (t1 - t0) / T_pre * 1e3, "smoother_ms_per_step": (t2 - t1) / (T_pre - 1) * 1e3}
+
+
+if __name__ == "__main__":
+    main()

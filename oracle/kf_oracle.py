@@ -47,7 +47,7 @@ import scipy.linalg as sla
 def dense_cov(kind: int, value, n: int) -> np.ndarray:
     """Covariance given as 0 = scalar * I, 1 = diagonal vector, 2 = dense."""
     if kind == 0:
-        return float(np.asarray(value)) * np.eye(n)
+        return float(np.asarray(value, dtype=np.float64).reshape(-1)[0]) * np.eye(n)
     if kind == 1:
         return np.diag(np.asarray(value, dtype=np.float64))
     return np.array(value, dtype=np.float64, copy=True)
