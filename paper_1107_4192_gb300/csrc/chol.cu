@@ -25,14 +25,15 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(T* A, int64_t lda, int 
   T* S = reinterpret_cast<T*>(smem_raw);
   T* X = S + NB * LD;
   __shared__ int fail;
-  if (status_failed(status)) return;
   const int tid = threadIdx.x, nt = blockDim.x;
+  if (tid == 0) fail = status_failed(status) ? 1 : 0;  // one read for the whole CTA
+  __syncthreads();
+  if (fail) return;
 
   for (int idx = tid; idx < n * n; idx += nt) {
     int i = idx / n, j = idx % n;
     S[i * LD + j] = (j <= i) ? A[(int64_t)i * lda + j] : T(0);
   }
-  if (tid == 0) fail = 0;
   __syncthreads();
 
   for (int j = 0; j < n; ++j) {

@@ -1,7 +1,7 @@
 // CUDA-core (FMA) tiled GEMM for float64 and float32 with the fused
 // covariance epilogue of ops.cuh.  Used for every float64 product of the
 // plain path, the float32 path, and the blocked Cholesky / triangular solves.
-#include "ops.cuh"
+#include "epilogue.cuh"
 
 namespace kfm {
 
@@ -17,13 +17,6 @@ template <> struct SimtCfg<float> {
   static constexpr int BM = 128, BN = 128, BK = 8, TM = 8, TN = 8, PAD = 4;
 };
 
-__device__ __forceinline__ double q_value(int q_kind, const double* q, int64_t ldq, int i, int j) {
-  if (q_kind == 0) return i == j ? q[0] : 0.0;
-  if (q_kind == 1) return i == j ? q[i] : 0.0;
-  if (q_kind == 2) return q[(int64_t)i * ldq + j];
-  return 0.0;
-}
-
 // Maps a linear block index onto the lower-triangular tile (tm >= tn).
 __device__ __forceinline__ void tri_tile(int b, int& tm, int& tn) {
   int r = (int)((sqrtf(8.0f * (float)b + 1.0f) - 1.0f) * 0.5f);
@@ -31,29 +24,6 @@ __device__ __forceinline__ void tri_tile(int b, int& tm, int& tn) {
   while (r * (r + 1) / 2 > b) --r;
   tm = r;
   tn = b - r * (r + 1) / 2;
-}
-
-template <typename T>
-__device__ __forceinline__ void epilogue_store(const GemmParams<T>& p, int gi, int gj, T acc) {
-  T vpre = p.alpha * acc;
-  if (p.cin) vpre += p.beta * p.cin[(int64_t)gi * p.ldcin + gj];
-  T v = vpre;
-  if (p.csub) v -= p.csub[(int64_t)gi * p.ldcsub + gj];
-  const bool mirror = (p.sym == 1) && gi != gj;
-  if (p.out) {
-    p.out[(int64_t)gi * p.ldo + gj] = v;
-    if (mirror) p.out[(int64_t)gj * p.ldo + gi] = v;
-  }
-  if (p.out2) {
-    T w = vpre + (T)q_value(p.q_kind, p.q, p.ldq, gi, gj);
-    p.out2[(int64_t)gi * p.ldo2 + gj] = w;
-    if (mirror) p.out2[(int64_t)gj * p.ldo2 + gi] = w;
-  }
-  if (gi == gj) {
-    if (p.diag_out) p.diag_out[gi] = (double)vpre;
-    if (p.check_diag && !(vpre > T(0) && isfinite((double)vpre)))
-      status_set(p.status, KF_ERR_NUMERIC, p.step, gi);
-  }
 }
 
 template <typename T, bool TB>
@@ -71,7 +41,10 @@ __global__ void __launch_bounds__(256) gemm_simt_kernel(GemmParams<T> p) {
     tn = blockIdx.x;
     tm = blockIdx.y;
   }
-  if (status_failed(p.status)) return;
+  __shared__ int skip;
+  if (threadIdx.x == 0) skip = status_failed(p.status) ? 1 : 0;  // one read for the whole CTA
+  __syncthreads();
+  if (skip) return;
   const int m0 = tm * BM, n0 = tn * BN;
   const int tid = threadIdx.x;
   const int tx = tid % 16, ty = tid / 16;

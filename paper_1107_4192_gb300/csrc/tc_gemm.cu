@@ -1,7 +1,354 @@
-// Placeholder until the tcgen05 kernel lands: reports the path as unavailable.
+// Split-bf16 ("bf16x3") GEMM on the 5th-generation tensor cores (tcgen05).
+//
+// C = A B^T for float32 A (M x K) and B (N x K).  Each operand is split into
+// bf16 planes hi = bf16(x), lo = bf16(x - hi); the product is accumulated as
+// hi(A) hi(B)^T + hi(A) lo(B)^T + lo(A) hi(B)^T in one float32 accumulator
+// held in tensor memory (TMEM), i.e. three bf16 MMAs per k-slice.  This is
+// how the mixed-precision path forms the N x N covariance products: the
+// smoother's W = J D and P + W J^T (eqn 13), the innovation U^T = P H^T
+// (eqn 8) and the update P - K U (eqn 10).
+//
+// Kernel structure (one 128 x BN output tile per CTA, 6 warps):
+//   warp 0  one lane issues TMA loads (cp.async.bulk.tensor, 128-byte
+//           swizzle) of the four operand tiles of a 64-wide k-slice into a
+//           shared-memory stage and arms the stage's "full" mbarrier;
+//   warp 1  allocates TMEM; one lane waits for "full", issues the 12
+//           tcgen05.mma (3 products x 4 k16 steps) and commits them to the
+//           stage's "empty" mbarrier, which hands the stage back to the TMA
+//           lane when the MMAs have read it; at the end it commits to the
+//           "accumulator ready" barrier;
+//   warps 2-5  read the accumulator with tcgen05.ld (each warp its 32 TMEM
+//           lanes = 32 rows) and apply the covariance epilogue.
+// Every mbarrier wait is bounded (about 2 s of %globaltimer); on expiry the
+// kernel raises KF_ERR_TIMEOUT in the status word, stops issuing, waits
+// (bounded) for what it already issued, frees TMEM and returns.
+#include <cuda.h>
+
+#include <mutex>
+
+#include "epilogue.cuh"
 #include "tc_gemm.cuh"
 
 namespace kfm {
+
+namespace {
+
+constexpr int BM = 128;
+constexpr int BK = 64;          // one 128-byte swizzle atom of bf16
+constexpr int UMMA_K = 16;
+constexpr int NUM_THREADS = 192;
+constexpr uint64_t WAIT_NS = 2000000000ull;
+
+template <int BN>
+struct TcCfg {
+  static constexpr int STAGES = BN == 256 ? 2 : 3;
+  static constexpr int A_BYTES = BM * BK * 2;   // one plane
+  static constexpr int B_BYTES = BN * BK * 2;
+  static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+  static constexpr int TMEM_COLS = BN;          // float32 accumulator, one column per output column
+  static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+  // instruction descriptor: D = f32, A = B = bf16, both K-major, N >> 3, M >> 4
+  static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                                    ((uint32_t)(BM >> 4) << 24);
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase; false on timeout or when another role aborted.
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+  uint64_t t0 = 0;
+  for (uint32_t it = 0;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 63u) == 63u) {
+      if (*abort_flag) return false;
+      const uint64_t now = globaltimer();
+      if (t0 == 0)
+        t0 = now;
+      else if (now - t0 > WAIT_NS)
+        return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor, K-major operand tile with 128-byte
+// swizzle: 8-row x 128-byte atoms stacked every 1024 bytes (SBO), LBO unused
+// for swizzled K-major tiles, fixed version field 0b001 at bits 46-48,
+// layout type 2 (SWIZZLE_128B) at bits 61-63.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;                  // LBO (ignored)
+  d |= (uint64_t)(1024 >> 4) << 32;        // SBO
+  d |= (uint64_t)1 << 46;                  // version
+  d |= (uint64_t)2 << 61;                  // SWIZZLE_128B
+  return d;
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+struct TcMaps {
+  CUtensorMap a_hi, a_lo, b_hi, b_lo;
+};
+
+template <int BN>
+__global__ void __launch_bounds__(NUM_THREADS, 1)
+    tc_gemm_kernel(const __grid_constant__ TcMaps maps, const GemmParams<float> p, int num_k_tiles) {
+  using C = TcCfg<BN>;
+  extern __shared__ uint8_t smem_raw[];
+  const int tn = blockIdx.x, tm = blockIdx.y;
+  const int m0 = tm * BM, n0 = tn * BN;
+  if (p.sym && m0 + BM - 1 < n0) return;  // tile entirely above the diagonal
+
+  const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  uint8_t* gbase = smem_raw + (base - smem_u32(smem_raw));
+  const uint32_t bars = base + C::STAGES * C::STAGE_BYTES;
+  auto full_bar = [&](int s) { return bars + 8u * s; };
+  auto empty_bar = [&](int s) { return bars + 8u * (C::STAGES + s); };
+  const uint32_t accum_bar = bars + 8u * (2 * C::STAGES);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + C::STAGES * C::STAGE_BYTES + 8 * (2 * C::STAGES + 1));
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  volatile int* skip_flag = reinterpret_cast<volatile int*>(tmem_slot + 2);
+  volatile int never = 0;  // abort flag for the clean-up waits, which must not stop early
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < C::STAGES; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    mbar_init(accum_bar, 1);
+    *abort_flag = 0;
+    *skip_flag = status_failed(p.status) ? 1 : 0;  // read once, shared by the whole CTA
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(C::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  const bool skip = *skip_flag != 0;
+
+  if (skip) {
+    // an earlier kernel failed: do nothing but release TMEM below
+  } else if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer
+    int last_round[4] = {-1, -1, -1, -1};
+    for (int kt = 0; kt < num_k_tiles; ++kt) {
+      const int s = kt % C::STAGES;
+      const uint32_t ph = (uint32_t)(kt / C::STAGES) & 1u;
+      if (!mbar_wait(empty_bar(s), ph ^ 1u, abort_flag)) {
+        *abort_flag = 1;
+        status_set(p.status, KF_ERR_TIMEOUT, p.step, 1);
+        break;
+      }
+      const uint32_t st = base + s * C::STAGE_BYTES;
+      mbar_expect_tx(full_bar(s), C::STAGE_BYTES);
+      const int x = kt * BK;
+      tma_load_2d(st, &maps.a_hi, x, m0, full_bar(s));
+      tma_load_2d(st + C::A_BYTES, &maps.a_lo, x, m0, full_bar(s));
+      tma_load_2d(st + 2 * C::A_BYTES, &maps.b_hi, x, n0, full_bar(s));
+      tma_load_2d(st + 2 * C::A_BYTES + C::B_BYTES, &maps.b_lo, x, n0, full_bar(s));
+      last_round[s] = kt / C::STAGES;
+    }
+    if (*abort_flag) {  // let issued copies land before the CTA's shared memory goes away
+      for (int s = 0; s < C::STAGES; ++s)
+        if (last_round[s] >= 0) mbar_wait(full_bar(s), (uint32_t)last_round[s] & 1u, &never);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    bool ok = true;
+    for (int kt = 0; kt < num_k_tiles; ++kt) {
+      const int s = kt % C::STAGES;
+      const uint32_t ph = (uint32_t)(kt / C::STAGES) & 1u;
+      if (!mbar_wait(full_bar(s), ph, abort_flag)) {
+        *abort_flag = 1;
+        status_set(p.status, KF_ERR_TIMEOUT, p.step, 2);
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t st = base + s * C::STAGE_BYTES;
+      const uint32_t a_hi = st, a_lo = st + C::A_BYTES;
+      const uint32_t b_hi = st + 2 * C::A_BYTES, b_lo = b_hi + C::B_BYTES;
+#pragma unroll
+      for (int k = 0; k < BK / UMMA_K; ++k) {
+        const uint32_t off = k * UMMA_K * 2;  // bytes along K inside the swizzle atom
+        const uint32_t acc = (kt > 0 || k > 0) ? 1u : 0u;
+        mma_bf16(tmem, smem_desc(a_hi + off), smem_desc(b_hi + off), C::IDESC, acc);
+        mma_bf16(tmem, smem_desc(a_hi + off), smem_desc(b_lo + off), C::IDESC, 1u);
+        mma_bf16(tmem, smem_desc(a_lo + off), smem_desc(b_hi + off), C::IDESC, 1u);
+      }
+      mma_commit(empty_bar(s));
+    }
+    mma_commit(accum_bar);
+    (void)ok;
+  } else if (warp >= 2) {
+    // ---------------- epilogue: warp w reads TMEM lanes 32*(w%4) .. +31
+    const int lane_base = 32 * (warp % 4);
+    bool ready = num_k_tiles > 0 ? mbar_wait(accum_bar, 0, abort_flag) : true;
+    if (!ready && !*abort_flag) {
+      *abort_flag = 1;
+      status_set(p.status, KF_ERR_TIMEOUT, p.step, 3);
+    }
+    if (ready) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int gi = m0 + lane_base + lane;
+#pragma unroll 1
+      for (int c = 0; c < BN; c += 32) {
+        uint32_t r[32];
+        if (num_k_tiles > 0) {
+          tmem_ld32(tmem + ((uint32_t)lane_base << 16) + (uint32_t)c, r);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) r[j] = 0u;
+        }
+        if (gi < p.M) {
+#pragma unroll 4
+          for (int j = 0; j < 32; ++j) {
+            const int gj = n0 + c + j;
+            if (gj >= p.N) break;
+            if (p.sym && gj > gi) break;
+            epilogue_store(p, gi, gj, __uint_as_float(r[j]));
+          }
+        }
+      }
+    }
+  }
+  // after an abort, make sure every issued MMA has finished before TMEM is freed
+  if (!skip && warp == 1 && lane == 0 && *abort_flag) mbar_wait(accum_bar, 0, &never);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TMEM_COLS)
+                 : "memory");
+  }
+}
+
+// ------------------------------------------------------------ host side
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(ptr);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+// rows x cols bf16 plane with leading dimension ld (elements), box = 64 x box_rows.
+kf_status make_map(CUtensorMap* map, const void* ptr, int64_t rows, int64_t cols, int64_t ld, int box_rows) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return KF_ERR_UNSUPPORTED;
+  if ((reinterpret_cast<uintptr_t>(ptr) & 15) || ((ld * 2) & 15) || cols % BK) return KF_ERR_ARG;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? KF_OK : KF_ERR_CUDA;
+}
+
+template <int BN>
+kf_status launch(cudaStream_t s, const GemmParams<float>& g, const __nv_bfloat16* a_hi, const __nv_bfloat16* a_lo,
+                 const __nv_bfloat16* b_hi, const __nv_bfloat16* b_lo, int64_t ldk) {
+  using C = TcCfg<BN>;
+  TcMaps maps;
+  KF_TRY(make_map(&maps.a_hi, a_hi, g.M, ldk, ldk, BM));
+  KF_TRY(make_map(&maps.a_lo, a_lo, g.M, ldk, ldk, BM));
+  KF_TRY(make_map(&maps.b_hi, b_hi, g.N, ldk, ldk, BN));
+  KF_TRY(make_map(&maps.b_lo, b_lo, g.N, ldk, ldk, BN));
+  static bool configured = false;
+  if (!configured) {
+    KF_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
+    configured = true;
+  }
+  dim3 grid((unsigned)ceil_div(g.N, BN), (unsigned)ceil_div(g.M, BM));
+  const int num_k_tiles = (int)(ldk / BK);
+  tc_gemm_kernel<BN><<<grid, NUM_THREADS, C::SMEM, s>>>(maps, g, num_k_tiles);
+  ++g_launches;
+  return launch_check("tc_gemm");
+}
+
+}  // namespace
 
 uint64_t tc_scratch_bytes(int64_t rows, int64_t ld) { return 4ull * rows * ld * sizeof(__nv_bfloat16); }
 
@@ -17,8 +364,35 @@ kf_status tc_scratch_alloc(TcScratch& sc, int64_t rows, int64_t ld,
   return KF_OK;
 }
 
-bool tc_available() { return false; }
+bool tc_available() {
+  int dev = 0, major = 0, minor = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return major == 10 && minor == 3 && encode_fn() != nullptr;
+}
 
-kf_status tc_gemm_bf16x3(cudaStream_t, TcScratch&, const GemmParams<float>&) { return KF_ERR_UNSUPPORTED; }
+kf_status tc_gemm_bf16x3(cudaStream_t s, TcScratch& sc, const GemmParams<float>& g) {
+  if (g.M <= 0 || g.N <= 0) return KF_OK;
+  if (g.sym && g.M != g.N) return KF_ERR_ARG;
+  const int64_t ldk = round_up(g.K > 0 ? g.K : 1, BK);
+  if (g.M > sc.rows || g.N > sc.rows || ldk > sc.ld) return KF_ERR_ARG;
+  if (g.K > 0) {
+    KF_TRY(split_bf16(s, g.M, g.K, g.A, g.lda, sc.a_hi, sc.a_lo, ldk));
+    KF_TRY(split_bf16(s, g.N, g.K, g.B, g.ldb, sc.b_hi, sc.b_lo, ldk));
+  }
+  GemmParams<float> h = g;
+  if (g.K == 0) {
+    // epilogue-only product: no operand tiles to load
+    return gemm_simt<float>(s, true, g);
+  }
+  return launch<256>(s, h, sc.a_hi, sc.a_lo, sc.b_hi, sc.b_lo, ldk);
+}
 
 }  // namespace kfm

@@ -143,3 +143,48 @@ def test_split_bf16():
     assert np.all(h[:, cols:] == 0) and np.all(lw[:, cols:] == 0)
     rel = np.abs(h[:, :cols] + lw[:, :cols] - A) / np.abs(A)
     assert rel.max() <= 2.0 ** -16
+
+
+def _split_ref(X):
+    """float64 values of the bf16 hi/lo planes of float32 X (round to nearest even)."""
+    t = torch.from_numpy(np.ascontiguousarray(X, np.float32))
+    hi = t.bfloat16().float()
+    lo = (t - hi).bfloat16().float()
+    return hi.double().numpy(), lo.double().numpy()
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 256, 64), (256, 256, 128), (130, 300, 200), (385, 129, 640), (1, 1, 1)])
+def test_tc_bf16x3_gemm(M, N, K):
+    """tcgen05 split-bf16 product vs the exact float64 value of the same three bf16 products."""
+    rng = np.random.default_rng(M + 7 * N + 13 * K)
+    A = rng.standard_normal((M, K)).astype(np.float32)
+    Bm = rng.standard_normal((N, K)).astype(np.float32)
+    C0 = rng.standard_normal((M, N)).astype(np.float32)
+    ah, al = _split_ref(A)
+    bh, bl = _split_ref(Bm)
+    exact = ah @ bh.T + ah @ bl.T + al @ bh.T
+    ref = -1.5 * exact + 0.5 * C0.astype(np.float64)
+    dC = torch.from_numpy(C0).cuda()
+    B.kfx_gemm(2, 1, 0, M, N, K, -1.5, torch.from_numpy(A).cuda(), K, torch.from_numpy(Bm).cuda(), K, 0.5, dC, N)
+    got = dC.double().cpu().numpy()
+    # only the float32 accumulation order differs from `exact`
+    assert np.abs(got - ref).max() <= 1e-5 * max(1.0, np.sqrt(K)) * np.abs(ref).max()
+    # and the product is float32-accurate against the float64 product of the inputs
+    full = -1.5 * A.astype(np.float64) @ Bm.astype(np.float64).T + 0.5 * C0
+    assert np.linalg.norm(got - full) <= 1e-4 * np.linalg.norm(full)
+
+
+@pytest.mark.parametrize("n,K", [(300, 64), (513, 320)])
+def test_tc_bf16x3_symmetric(n, K):
+    rng = np.random.default_rng(n)
+    A = rng.standard_normal((n, K)).astype(np.float32)
+    Bm = rng.standard_normal((n, K)).astype(np.float32)
+    S0 = rng.standard_normal((n, n)).astype(np.float32)
+    S0 = S0 + S0.T
+    dC = torch.from_numpy(S0).cuda()
+    B.kfx_gemm(2, 1, 1, n, n, K, 1.0, torch.from_numpy(A).cuda(), K, torch.from_numpy(Bm).cuda(), K, 1.0, dC, n)
+    got = dC.double().cpu().numpy()
+    assert np.array_equal(got, got.T)
+    ref = A.astype(np.float64) @ Bm.astype(np.float64).T + S0
+    low = np.tril(np.ones((n, n), bool))
+    assert np.abs(got - ref)[low].max() <= 1e-4 * np.abs(ref).max()

@@ -66,6 +66,15 @@ def test_fp32_paths(solve, mesh):
     check(solver.run(prob, prec=B.KF_PREC_FP32, solve_prec=solve), run_oracle(prob), TOL_MEAN32, TOL_DIAG32)
 
 
+@pytest.mark.parametrize("solve", [B.KF_SOLVE_FP64, B.KF_SOLVE_FP32])
+@pytest.mark.parametrize("mesh", [False, True])
+def test_mixed_bf16x3_paths(solve, mesh):
+    """Split-bf16 tensor-core products with float32 accumulation, Joseph form every 4 steps."""
+    prob = synth.mesh_problem(324, 30, 12, seed=4) if mesh else synth.random_walk_problem(384, 64, 20, seed=0)
+    out = solver.run(prob, prec=B.KF_PREC_MIXED_BF16X3, solve_prec=solve, joseph_every=4)
+    check(out, run_oracle(prob), TOL_MEAN32, TOL_DIAG32)
+
+
 def test_joseph_every_k_fp64():
     prob = synth.random_dense_problem(130, 20, 10, seed=9)
     check(solver.run(prob, prec=B.KF_PREC_FP64, joseph_every=3), run_oracle(prob), TOL64, TOL64)
