@@ -56,8 +56,10 @@ typedef enum { KF_F_IDENTITY = 0, KF_F_CSR = 1, KF_F_DENSE = 2 } kf_f_kind;
 typedef enum {
   KF_PREC_FP64 = 0,          /* float64 everywhere                                   */
   KF_PREC_FP32 = 1,          /* float32 products, float32 store                      */
-  KF_PREC_MIXED_BF16X3 = 2   /* split-bf16 (hi*hi + hi*lo + lo*hi) tensor-core       */
-                             /* products, fp32 accumulate, float32 store             */
+  KF_PREC_MIXED_BF16X3 = 2   /* split-bf16 tensor-core products, fp32 accumulate,    */
+                             /* float32 store: the smoother's N x N covariance       */
+                             /* products as hi*hi + hi*lo + lo*hi (see split_terms), */
+                             /* the filter's products with a three-way split         */
 } kf_precision;
 
 /* Arithmetic of the smoother-gain solve J_t = P_{t|t} F^T P_{t+1|t}^{-1}
@@ -84,7 +86,9 @@ typedef struct {
   uint64_t mem_budget_bytes; /* cap on plan-owned device memory; 0 = no cap          */
   int32_t checkpoint_every;  /* 0 = chosen from the budget; c > 0 forces keeping     */
                              /* every c-th P_{t|t} and recomputing the rest          */
-  int32_t reserved;
+  int32_t split_terms;       /* KF_PREC_MIXED_BF16X3 only: bf16 products per product */
+                             /* in the smoother's covariance GEMMs, 3 (hi/lo split,  */
+                             /* default when 0) or 6 (three-way split, float32-class) */
   void* stream;              /* cudaStream_t for all work of this plan               */
 } kf_desc;
 

@@ -31,7 +31,7 @@ class KfDesc(ctypes.Structure):
                 ("f_kind", ctypes.c_int32), ("prec", ctypes.c_int32), ("solve_prec", ctypes.c_int32),
                 ("q_kind", ctypes.c_int32), ("r_kind", ctypes.c_int32), ("joseph_every", ctypes.c_int32),
                 ("f_nnz", ctypes.c_int64), ("mem_budget_bytes", ctypes.c_uint64),
-                ("checkpoint_every", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("checkpoint_every", ctypes.c_int32), ("split_terms", ctypes.c_int32),
                 ("stream", ctypes.c_void_p)]
 
 
@@ -129,9 +129,9 @@ def _check(st: int, where: str, fail_step: int = 0):
 
 def make_desc(N, m, T, f_kind=KF_F_IDENTITY, prec=KF_PREC_FP64, solve_prec=KF_SOLVE_FP64,
               q_kind=KF_COV_SCALAR, r_kind=KF_COV_SCALAR, joseph_every=0, f_nnz=0,
-              mem_budget_bytes=0, checkpoint_every=0, stream=None) -> KfDesc:
+              mem_budget_bytes=0, checkpoint_every=0, split_terms=0, stream=None) -> KfDesc:
     return KfDesc(N, m, T, f_kind, prec, solve_prec, q_kind, r_kind, joseph_every, f_nnz,
-                  mem_budget_bytes, checkpoint_every, 0, _stream(stream))
+                  mem_budget_bytes, checkpoint_every, split_terms, _stream(stream))
 
 
 def kf_plan_footprint(desc: KfDesc):

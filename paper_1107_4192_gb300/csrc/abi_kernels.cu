@@ -41,8 +41,7 @@ kf_status kfx_gemm(int32_t dtype, int32_t transB, int32_t sym, int64_t M, int64_
     st = gemm_typed<double>(dtype, transB, sym, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s);
   } else if (dtype == 1) {
     st = gemm_typed<float>(dtype, transB, sym, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s);
-  } else if (dtype == 2) {
-    if (!transB) return KF_ERR_ARG;
+  } else if (dtype == 2 || dtype == 3) {
     if (!tc_available()) return KF_ERR_UNSUPPORTED;
     GemmParams<float> g;
     g.M = (int)M; g.N = (int)N; g.K = (int)K;
@@ -63,7 +62,7 @@ kf_status kfx_gemm(int32_t dtype, int32_t transB, int32_t sym, int64_t M, int64_
       mem.push_back(*ptr);
       return KF_OK;
     });
-    if (st == KF_OK) st = tc_gemm_bf16x3(s, sc, g);
+    if (st == KF_OK) st = tc_gemm_split(s, sc, g, dtype == 2 ? 2 : 3, transB != 0);
     cudaStreamSynchronize(s);
     for (void* p : mem) cudaFree(p);
   } else {
@@ -141,7 +140,8 @@ kf_status kfx_split_bf16(int64_t rows, int64_t cols, const float* A, int64_t lda
                          void* stream) {
   if (rows < 0 || cols < 0 || ldh < cols || !A || !hi || !lo) return KF_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
-  KF_TRY(split_bf16(s, rows, cols, A, lda, (__nv_bfloat16*)hi, (__nv_bfloat16*)lo, ldh));
+  __nv_bfloat16* planes[2] = {(__nv_bfloat16*)hi, (__nv_bfloat16*)lo};
+  KF_TRY(split_bf16(s, rows, cols, A, lda, planes, 2, ldh));
   KF_CUDA_TRY(cudaStreamSynchronize(s));
   return KF_OK;
 }

@@ -18,8 +18,8 @@ template <> int potrf_block<float>() { return 128; }
 // Factors the n x n (n <= NB) lower triangle at A in shared memory, writes L
 // back (lower triangle only) and L^{-1} to dinv (NB x NB, zero above the diagonal).
 template <typename T, int NB>
-__global__ void __launch_bounds__(256) potrf_diag_kernel(T* A, int64_t lda, int n, T* dinv, int* status,
-                                                         int step, int base) {
+__global__ void __launch_bounds__(256) potrf_diag_kernel(T* A, int64_t lda, int n, T* dinv, int64_t ldd,
+                                                         int* status, int step, int base) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int LD = NB + 1;
   T* S = reinterpret_cast<T*>(smem_raw);
@@ -86,14 +86,14 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(T* A, int64_t lda, int 
     }
   }
   __syncthreads();
-  for (int idx = tid; idx < NB * NB; idx += nt) {
-    int i = idx / NB, j = idx % NB;
-    dinv[idx] = (i < n && j < n && j <= i) ? X[i * LD + j] : T(0);
+  for (int idx = tid; idx < n * n; idx += nt) {
+    int i = idx / n, j = idx % n;
+    dinv[(int64_t)i * ldd + j] = j <= i ? X[i * LD + j] : T(0);
   }
 }
 
 template <typename T, int NB>
-static kf_status launch_potrf_diag(cudaStream_t s, T* A, int64_t lda, int n, T* dinv, int* status,
+static kf_status launch_potrf_diag(cudaStream_t s, T* A, int64_t lda, int n, T* dinv, int64_t ldd, int* status,
                                    int step, int base) {
   const size_t smem = 2ull * NB * (NB + 1) * sizeof(T);
   static bool configured = false;
@@ -102,9 +102,17 @@ static kf_status launch_potrf_diag(cudaStream_t s, T* A, int64_t lda, int n, T* 
                          (int)smem);
     configured = true;
   }
-  potrf_diag_kernel<T, NB><<<1, 256, smem, s>>>(A, lda, n, dinv, status, step, base);
+  potrf_diag_kernel<T, NB><<<1, 256, smem, s>>>(A, lda, n, dinv, ldd, status, step, base);
   ++g_launches;
   return launch_check("potrf_diag");
+}
+
+template <typename T>
+kf_status potrf_diag(cudaStream_t s, T* A, int64_t lda, int n, T* dinv, int64_t ldd, int* status, int step,
+                     int base) {
+  if (n <= 64) return launch_potrf_diag<T, 64>(s, A, lda, n, dinv, ldd, status, step, base);
+  if (sizeof(T) == 8 || n > 128) return KF_ERR_ARG;
+  return launch_potrf_diag<T, 128>(s, A, lda, n, dinv, ldd, status, step, base);
 }
 
 template <typename T>
@@ -114,10 +122,7 @@ kf_status potrf(cudaStream_t s, T* A, int64_t lda, int n, T* dinv, int nb, int* 
     const int kb = n - k < nb ? n - k : nb;
     T* Akk = A + (int64_t)k * lda + k;
     T* Dk = dinv + (int64_t)(k / nb) * nb * nb;
-    if (nb == 64)
-      KF_TRY((launch_potrf_diag<T, 64>(s, Akk, lda, kb, Dk, status, step, k)));
-    else
-      KF_TRY((launch_potrf_diag<T, 128>(s, Akk, lda, kb, Dk, status, step, k)));
+    KF_TRY(potrf_diag<T>(s, Akk, lda, kb, Dk, nb, status, step, k));
     const int rest = n - k - kb;
     if (rest <= 0) break;
     // panel: L21 = A21 L11^{-T}  (C[r][c] = sum_j A21[r][j] Linv[c][j]); one column tile
@@ -198,6 +203,8 @@ kf_status trsm_right(cudaStream_t s, bool trans, int M, int n, const T* L, int64
   return KF_OK;
 }
 
+template kf_status potrf_diag<double>(cudaStream_t, double*, int64_t, int, double*, int64_t, int*, int, int);
+template kf_status potrf_diag<float>(cudaStream_t, float*, int64_t, int, float*, int64_t, int*, int, int);
 template kf_status potrf<double>(cudaStream_t, double*, int64_t, int, double*, int, int*, int);
 template kf_status potrf<float>(cudaStream_t, float*, int64_t, int, float*, int, int*, int);
 template kf_status trsm_right<double>(cudaStream_t, bool, int, int, const double*, int64_t,

@@ -42,6 +42,12 @@ struct GemmParams {
   int check_diag = 0;
   int step = 0;
   int sym = 0;
+  // Tensor-core path only: transA = 1 means A is stored K x M (row-major) and
+  // is used transposed.  tri_a / tri_b: +1 when row r of the operand as used
+  // (A: M x K, op(B): N x K) is zero for k > r, -1 when zero for k < r, so
+  // k-tiles outside the band are skipped; 0 = dense.
+  int transA = 0;
+  int tri_a = 0, tri_b = 0;
 };
 
 // C = op(A) x op(B) with A: M x K row-major; B: N x K row-major when transB
@@ -59,6 +65,13 @@ kf_status potrf(cudaStream_t s, T* A, int64_t lda, int n, T* dinv, int nb, int* 
 
 template <typename T>
 int potrf_block();  // the nb used by potrf for dtype T
+
+// One diagonal block (n <= 64 for float64, <= 128 for float32): L = chol(A)
+// in place (lower triangle) and L^{-1} written to dinv (leading dimension
+// ldd, zero above the diagonal).  base = index of the block's first pivot.
+template <typename T>
+kf_status potrf_diag(cudaStream_t s, T* A, int64_t lda, int n, T* dinv, int64_t ldd, int* status, int step,
+                     int base);
 
 // B <- B L^{-T} (trans = true) or B <- B L^{-1} (trans = false), B: M x n,
 // L: n x n lower triangular from potrf with its diagonal-block inverses dinv.
@@ -114,10 +127,16 @@ template <typename T>
 kf_status spmm_pft(cudaStream_t s, int64_t N, const int64_t* rowptr, const int64_t* col,
                    const double* val, const T* P, int64_t ldp, T* out, int64_t ldo);
 
-// Splits float A (rows x cols, lda) into bf16 planes hi = bf16(A), lo = bf16(A - hi);
-// columns cols..ldh-1 of both planes are zeroed.
+// Splits float A (rows x cols, lda) into `n` (2 or 3) bf16 planes:
+// plane k = bf16(A - plane 0 - .. - plane k-1) (round to nearest); columns
+// cols..ldh-1 of every plane are zeroed.
 kf_status split_bf16(cudaStream_t s, int64_t rows, int64_t cols, const float* A, int64_t lda,
-                     __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t ldh);
+                     __nv_bfloat16* const* planes, int n, int64_t ldh);
+
+// As split_bf16 for the transpose: plane[r][k] = split(A[k][r]) for r < rows,
+// k < cols, where A is cols x rows with leading dimension lda.
+kf_status split_bf16_t(cudaStream_t s, int64_t rows, int64_t cols, const float* A, int64_t lda,
+                       __nv_bfloat16* const* planes, int n, int64_t ldh);
 
 // diag_out[i] = A[i, i]
 template <typename T>

@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "ops.cuh"
+#include "solve_tc.cuh"
 #include "tc_gemm.cuh"
 
 using namespace kfm;
@@ -40,6 +41,7 @@ struct kf_plan_s {
   cudaStream_t s = nullptr;
   int64_t N = 0, m = 0, T = 0, ldN = 0, ldm = 0;
   int bulk = 0, solve = 0;
+  int smooth_slices = 2;  // bf16 planes per operand in the smoother products (mixed mode)
   size_t b = 8, sb = 8;   // bytes per bulk / solve element
   int64_t ckpt = 1;       // 1 = every P_{t|t} stored
   int64_t nck = 0;        // checkpoint slots
@@ -55,6 +57,7 @@ struct kf_plan_s {
   double *S = nullptr, *S0 = nullptr, *Sdinv = nullptr, *partials = nullptr;
   char *Sl = nullptr, *Sldinv = nullptr;
   char *Lb = nullptr, *Ldinv = nullptr, *Jb = nullptr;
+  float* Wi = nullptr;    // L^{-1} for the tensor-core solve (mixed mode, float32 solve)
   char *Jm = nullptr, *Wb = nullptr, *Db = nullptr, *Pn = nullptr;
   TcScratch tc{};
   double *F = nullptr, *Q = nullptr, *H = nullptr, *R = nullptr;
@@ -107,6 +110,7 @@ Sizes sizes_for(const kf_desc* d) {
   const int64_t nbs = z.sb == 8 ? 64 : 128;
   w += 2 * N * ldN * z.sb + round_up(N, nbs) * nbs * z.sb;                 // Lb, Jb, Ldinv
   w += (z.sb != z.b ? z.slot : 0) + 3 * z.slot;                            // Jm, Wb, Db, Pn
+  if (d->prec == KF_PREC_MIXED_BF16X3 && z.sb == 4) w += z.slot;         // Wi
   w += 3 * (T + 1) * N * 8 + m * 8 + N * 8;                                // means
   if (d->f_kind == KF_F_CSR) w += d->f_nnz * 16 + (N + 1) * 8;
   if (d->f_kind == KF_F_DENSE) w += N * N * 8 + z.slot;
@@ -127,6 +131,7 @@ kf_status validate(const kf_desc* d) {
   if (d->solve_prec < 0 || d->solve_prec > 1) return KF_ERR_ARG;
   if (d->q_kind < 0 || d->q_kind > 2 || d->r_kind < 0 || d->r_kind > 2) return KF_ERR_ARG;
   if (d->joseph_every < 0 || d->checkpoint_every < 0) return KF_ERR_ARG;
+  if (d->split_terms != 0 && d->split_terms != 3 && d->split_terms != 6) return KF_ERR_ARG;
   return KF_OK;
 }
 
@@ -211,17 +216,21 @@ struct Prof {
 
 // ------------------------------------------------------------ GEMM dispatch
 
+// Bulk products: float64 / float32 on the CUDA cores, or split-bf16 on the
+// tensor cores in the mixed mode (`slices` bf16 planes per operand: 2 for
+// the smoother's covariance products by default, 3 where cancellation makes
+// float32-class products necessary, as in the filter update P - K U).
 template <typename B>
-kf_status gemm_bulk(kf_plan_s* p, bool transB, const GemmParams<B>& g);
+kf_status gemm_bulk(kf_plan_s* p, bool transB, const GemmParams<B>& g, int slices);
 
 template <>
-kf_status gemm_bulk<double>(kf_plan_s* p, bool transB, const GemmParams<double>& g) {
+kf_status gemm_bulk<double>(kf_plan_s* p, bool transB, const GemmParams<double>& g, int) {
   return gemm_simt<double>(p->s, transB, g);
 }
 
 template <>
-kf_status gemm_bulk<float>(kf_plan_s* p, bool transB, const GemmParams<float>& g) {
-  if (p->bulk == BULK_BF16X3 && transB) return tc_gemm_bf16x3(p->s, p->tc, g);
+kf_status gemm_bulk<float>(kf_plan_s* p, bool transB, const GemmParams<float>& g, int slices) {
+  if (p->bulk == BULK_BF16X3 && transB) return tc_gemm_split(p->s, p->tc, g, slices);
   return gemm_simt<float>(p->s, transB, g);
 }
 
@@ -274,7 +283,7 @@ kf_status filter_step(kf_plan_s* p, int64_t t, const double* y, double* diag_out
     g.B = (const B*)p->Hb; g.ldb = ldN;
     g.out = Ut; g.ldo = ldm;
     g.status = p->status;
-    KF_TRY(gemm_bulk<B>(p, true, g));
+    KF_TRY(gemm_bulk<B>(p, true, g, 3));
   }
   // S = H U^T + R (float64), then its Cholesky factor in place
   KF_TRY(innovation_cov<B>(s, m, N, p->H, N, Ut, ldm, p->d.r_kind, p->R, p->S, m, p->partials, kSplitsS));
@@ -339,7 +348,7 @@ kf_status filter_step(kf_plan_s* p, int64_t t, const double* y, double* diag_out
   }
   {
     Prof pr(p, KF_KC_FILTER_UPDATE);
-    KF_TRY(gemm_bulk<B>(p, true, u));
+    KF_TRY(gemm_bulk<B>(p, true, u, 3));
   }
   if (!ident) KF_TRY(predict_cov<B>(p, dst, P));
   return KF_OK;
@@ -427,15 +436,19 @@ kf_status run_smoother(kf_plan_s* p, double* x_smooth, double* diagP_smooth, dou
       Prof pr(p, KF_KC_SMOOTH_SOLVE);
       // P_{t+1|t} = L L^T
       KF_TRY((copy2d<V, B>(s, Lb, ldN, Pn, ldN, N, N)));
-      KF_TRY(potrf<V>(s, Lb, ldN, (int)N, (V*)p->Ldinv, nbs, p->status, (int)(t + 1)));
+      const bool tc_solve = p->bulk == BULK_BF16X3 && sizeof(V) == 4;
+      if (tc_solve)
+        KF_TRY(chol_inverse_tc(s, p->tc, (int)N, (float*)Lb, ldN, p->Wi, ldN, (float*)p->tmpN, ldN, p->status,
+                               (int)(t + 1)));
+      else
+        KF_TRY(potrf<V>(s, Lb, ldN, (int)N, (V*)p->Ldinv, nbs, p->status, (int)(t + 1)));
       KF_TRY(get_P<B>(p, t, &Pt));
-      // J_t = P_{t|t} F^T L^{-T} L^{-1}
-      if (p->d.f_kind == KF_F_IDENTITY) {
-        KF_TRY((copy2d<V, B>(s, Jb, ldN, Pt, ldN, N, N)));
-      } else if (p->d.f_kind == KF_F_CSR) {
+      // J_t = P_{t|t} F^T P_{t+1|t}^{-1}
+      const B* Bm = Pt;
+      if (p->d.f_kind == KF_F_CSR) {
         KF_TRY(spmm_pft<B>(s, N, p->Frp, p->Fcol, p->F, Pt, ldN, (B*)p->tmpN, ldN));
-        KF_TRY((copy2d<V, B>(s, Jb, ldN, (const B*)p->tmpN, ldN, N, N)));
-      } else {
+        Bm = (const B*)p->tmpN;
+      } else if (p->d.f_kind == KF_F_DENSE) {
         GemmParams<B> f;
         f.M = (int)N; f.N = (int)N; f.K = (int)N;
         f.A = Pt; f.lda = ldN;
@@ -443,10 +456,20 @@ kf_status run_smoother(kf_plan_s* p, double* x_smooth, double* diagP_smooth, dou
         f.out = (B*)p->tmpN; f.ldo = ldN;
         f.status = p->status;
         KF_TRY(gemm_simt<B>(s, true, f));
-        KF_TRY((copy2d<V, B>(s, Jb, ldN, (const B*)p->tmpN, ldN, N, N)));
+        Bm = (const B*)p->tmpN;
       }
-      KF_TRY(trsm_right<V>(s, true, (int)N, (int)N, Lb, ldN, (const V*)p->Ldinv, nbs, Jb, ldN, p->status));
-      KF_TRY(trsm_right<V>(s, false, (int)N, (int)N, Lb, ldN, (const V*)p->Ldinv, nbs, Jb, ldN, p->status));
+      if (tc_solve) {
+        if (Bm != Pt) {  // Bm lives in tmpN, which the products below use as scratch
+          KF_TRY((copy2d<B, B>(s, (B*)Jb, ldN, Bm, ldN, N, N)));
+          Bm = (const B*)Jb;
+        }
+        KF_TRY(gain_from_inverse_tc(s, p->tc, (int)N, (const float*)Bm, ldN, p->Wi, ldN, (float*)p->tmpN, ldN,
+                                    (float*)Jb, ldN, p->status));
+      } else {
+        KF_TRY((copy2d<V, B>(s, Jb, ldN, Bm, ldN, N, N)));
+        KF_TRY(trsm_right<V>(s, true, (int)N, (int)N, Lb, ldN, (const V*)p->Ldinv, nbs, Jb, ldN, p->status));
+        KF_TRY(trsm_right<V>(s, false, (int)N, (int)N, Lb, ldN, (const V*)p->Ldinv, nbs, Jb, ldN, p->status));
+      }
     }
     // x_{t|T} = x_{t|t} + J_t (x_{t+1|T} - x_{t+1|t})
     KF_TRY(vsub(s, N, p->xs + (t + 1) * N, p->xpred + (t + 1) * N, p->dx));
@@ -460,7 +483,7 @@ kf_status run_smoother(kf_plan_s* p, double* x_smooth, double* diagP_smooth, dou
       w.B = Db; w.ldb = ldN;
       w.out = Wb; w.ldo = ldN;
       w.status = p->status;
-      KF_TRY(gemm_bulk<B>(p, true, w));
+      KF_TRY(gemm_bulk<B>(p, true, w, p->smooth_slices));
     }
     const B* Ptm1;
     KF_TRY(get_P<B>(p, t - 1, &Ptm1));
@@ -482,7 +505,7 @@ kf_status run_smoother(kf_plan_s* p, double* x_smooth, double* diagP_smooth, dou
       g.step = (int)t;
       g.sym = 1;
       g.status = p->status;
-      KF_TRY(gemm_bulk<B>(p, true, g));
+      KF_TRY(gemm_bulk<B>(p, true, g, p->smooth_slices));
     }
     if (P_full && t_full == t) KF_TRY((copy2d<double, B>(s, P_full, N, (const B*)p->tmpN, ldN, N, N)));
   }
@@ -551,6 +574,7 @@ kf_status kf_plan(kf_plan_t* out, const kf_desc* d) {
   p->b = z.b; p->sb = z.sb;
   p->bulk = d->prec == KF_PREC_FP64 ? BULK_F64 : d->prec == KF_PREC_FP32 ? BULK_F32 : BULK_BF16X3;
   p->solve = z.sb == 8 ? 0 : 1;
+  p->smooth_slices = d->split_terms == 6 ? 3 : 2;
   p->slot = z.slot;
   p->ckpt = c;
   p->launches0 = g_launches;
@@ -586,6 +610,7 @@ kf_status kf_plan(kf_plan_t* out, const kf_desc* d) {
   A(&p->Jb, N * ldN * sb);
   A(&p->Ldinv, round_up(N, nbs) * nbs * sb);
   if (sb != b) A(&p->Jm, p->slot);
+  if (p->bulk == BULK_BF16X3 && sb == 4) A(&p->Wi, p->slot);
   A(&p->Wb, p->slot);
   A(&p->Db, p->slot);
   A(&p->Pn, p->slot);

@@ -212,25 +212,67 @@ kf_status predict_mean(cudaStream_t s, int f_kind, int64_t N, const double* F, c
   return gemv<double>(s, N, N, F, N, x, nullptr, 1.0, x_out);
 }
 
-__global__ void split_bf16_kernel(int64_t rows, int64_t cols, const float* A, int64_t lda, __nv_bfloat16* hi,
-                                  __nv_bfloat16* lo, int64_t ldh) {
+struct Planes3 {
+  __nv_bfloat16* p[3];
+};
+
+__global__ void split_bf16_kernel(int64_t rows, int64_t cols, const float* A, int64_t lda, Planes3 pl, int n,
+                                  int64_t ldh) {
   for (int64_t i = blockIdx.y; i < rows; i += gridDim.y)
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < ldh; j += (int64_t)gridDim.x * blockDim.x) {
-      float a = j < cols ? A[i * lda + j] : 0.0f;
-      __nv_bfloat16 h = __float2bfloat16_rn(a);
-      __nv_bfloat16 l = __float2bfloat16_rn(a - __bfloat162float(h));
-      hi[i * ldh + j] = h;
-      lo[i * ldh + j] = l;
+      float r = j < cols ? A[i * lda + j] : 0.0f;
+      for (int k = 0; k < n; ++k) {
+        __nv_bfloat16 h = __float2bfloat16_rn(r);
+        pl.p[k][i * ldh + j] = h;
+        r -= __bfloat162float(h);  // exact: r and h agree in their leading bits
+      }
     }
 }
 
 kf_status split_bf16(cudaStream_t s, int64_t rows, int64_t cols, const float* A, int64_t lda,
-                     __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t ldh) {
+                     __nv_bfloat16* const* planes, int n, int64_t ldh) {
   if (rows <= 0) return KF_OK;
+  if (n < 1 || n > 3) return KF_ERR_ARG;
+  Planes3 pl{{planes[0], n > 1 ? planes[1] : nullptr, n > 2 ? planes[2] : nullptr}};
   dim3 grid((unsigned)std::min<int64_t>(ceil_div(ldh, 256), 64), (unsigned)std::min<int64_t>(rows, 65535));
-  split_bf16_kernel<<<grid, 256, 0, s>>>(rows, cols, A, lda, hi, lo, ldh);
+  split_bf16_kernel<<<grid, 256, 0, s>>>(rows, cols, A, lda, pl, n, ldh);
   ++g_launches;
   return launch_check("split_bf16");
+}
+
+// Transposed split through a 32 x 32 shared-memory tile: reads rows of A
+// (coalesced) and writes rows of the planes (coalesced).
+__global__ void split_bf16_t_kernel(int64_t rows, int64_t cols, const float* A, int64_t lda, Planes3 pl, int n,
+                                    int64_t ldh) {
+  __shared__ float tile[32][33];
+  const int64_t r0 = (int64_t)blockIdx.x * 32, k0 = (int64_t)blockIdx.y * 32;
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;  // 32 x 8 threads
+  for (int i = ty; i < 32; i += 8) {
+    const int64_t k = k0 + i, r = r0 + tx;
+    tile[i][tx] = (k < cols && r < rows) ? A[k * lda + r] : 0.0f;
+  }
+  __syncthreads();
+  for (int i = ty; i < 32; i += 8) {
+    const int64_t r = r0 + i, k = k0 + tx;
+    if (r >= rows || k >= ldh) continue;
+    float v = tile[tx][i];
+    for (int s = 0; s < n; ++s) {
+      __nv_bfloat16 h = __float2bfloat16_rn(v);
+      pl.p[s][r * ldh + k] = h;
+      v -= __bfloat162float(h);
+    }
+  }
+}
+
+kf_status split_bf16_t(cudaStream_t s, int64_t rows, int64_t cols, const float* A, int64_t lda,
+                       __nv_bfloat16* const* planes, int n, int64_t ldh) {
+  if (rows <= 0) return KF_OK;
+  if (n < 1 || n > 3 || ceil_div(rows, 32) > 0x7fffffff || ceil_div(ldh, 32) > 65535) return KF_ERR_ARG;
+  Planes3 pl{{planes[0], n > 1 ? planes[1] : nullptr, n > 2 ? planes[2] : nullptr}};
+  dim3 grid((unsigned)ceil_div(rows, 32), (unsigned)ceil_div(ldh, 32));
+  split_bf16_t_kernel<<<grid, 256, 0, s>>>(rows, cols, A, lda, pl, n, ldh);
+  ++g_launches;
+  return launch_check("split_bf16_t");
 }
 
 template <typename T>

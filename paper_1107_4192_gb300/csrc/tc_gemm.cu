@@ -1,9 +1,11 @@
-// Split-bf16 ("bf16x3") GEMM on the 5th-generation tensor cores (tcgen05).
+// Split-bf16 GEMM on the 5th-generation tensor cores (tcgen05).
 //
 // C = A B^T for float32 A (M x K) and B (N x K).  Each operand is split into
-// bf16 planes hi = bf16(x), lo = bf16(x - hi); the product is accumulated as
-// hi(A) hi(B)^T + hi(A) lo(B)^T + lo(A) hi(B)^T in one float32 accumulator
-// held in tensor memory (TMEM), i.e. three bf16 MMAs per k-slice.  This is
+// S bf16 planes x = x_0 + x_1 (+ x_2), x_k = bf16(x - x_0 - .. - x_{k-1});
+// the products A_i B_j^T with i + j < S are accumulated in one float32
+// accumulator held in tensor memory (TMEM).  S = 2 is "bf16x3"
+// (hi hi + hi lo + lo hi, about 16 significant bits); S = 3 is "bf16x6"
+// (six products, about 24 bits, float32-class).  This is
 // how the mixed-precision path forms the N x N covariance products: the
 // smoother's W = J D and P + W J^T (eqn 13), the innovation U^T = P H^T
 // (eqn 8) and the update P - K U (eqn 10).
@@ -39,12 +41,13 @@ constexpr int UMMA_K = 16;
 constexpr int NUM_THREADS = 192;
 constexpr uint64_t WAIT_NS = 2000000000ull;
 
-template <int BN>
+template <int BN, int S>  // S = bf16 slices per operand: 2 -> 3 products, 3 -> 6 products
 struct TcCfg {
-  static constexpr int STAGES = BN == 256 ? 2 : 3;
   static constexpr int A_BYTES = BM * BK * 2;   // one plane
   static constexpr int B_BYTES = BN * BK * 2;
-  static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+  static constexpr int STAGE_BYTES = S * A_BYTES + S * B_BYTES;
+  static constexpr int STAGES = (200 * 1024) / STAGE_BYTES;
+  static_assert(STAGES >= 2, "need a double-buffered pipeline");
   static constexpr int TMEM_COLS = BN;          // float32 accumulator, one column per output column
   static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
   // instruction descriptor: D = f32, A = B = bf16, both K-major, N >> 3, M >> 4
@@ -147,13 +150,13 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 }
 
 struct TcMaps {
-  CUtensorMap a_hi, a_lo, b_hi, b_lo;
+  CUtensorMap a[3], b[3];  // bf16 planes of A and B, most significant first
 };
 
-template <int BN>
+template <int BN, int S>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ TcMaps maps, const GemmParams<float> p, int num_k_tiles) {
-  using C = TcCfg<BN>;
+  using C = TcCfg<BN, S>;
   extern __shared__ uint8_t smem_raw[];
   const int tn = blockIdx.x, tm = blockIdx.y;
   const int m0 = tm * BM, n0 = tn * BN;
@@ -192,15 +195,23 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
   const bool skip = *skip_flag != 0;
+  // k-tile band of this output tile (triangular operands contribute nothing outside it)
+  int kt0 = 0, kt1 = num_k_tiles;
+  if (p.tri_a > 0) kt1 = min(kt1, (m0 + BM + BK - 1) / BK);
+  if (p.tri_a < 0) kt0 = max(kt0, m0 / BK);
+  if (p.tri_b > 0) kt1 = min(kt1, (n0 + BN + BK - 1) / BK);
+  if (p.tri_b < 0) kt0 = max(kt0, n0 / BK);
+  const int nk = kt1 > kt0 ? kt1 - kt0 : 0;
 
   if (skip) {
     // an earlier kernel failed: do nothing but release TMEM below
   } else if (warp == 0 && lane == 0) {
     // ---------------- TMA producer
-    int last_round[4] = {-1, -1, -1, -1};
-    for (int kt = 0; kt < num_k_tiles; ++kt) {
-      const int s = kt % C::STAGES;
-      const uint32_t ph = (uint32_t)(kt / C::STAGES) & 1u;
+    int last_round[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
+    for (int it = 0; it < nk; ++it) {
+      const int kt = kt0 + it;
+      const int s = it % C::STAGES;
+      const uint32_t ph = (uint32_t)(it / C::STAGES) & 1u;
       if (!mbar_wait(empty_bar(s), ph ^ 1u, abort_flag)) {
         *abort_flag = 1;
         status_set(p.status, KF_ERR_TIMEOUT, p.step, 1);
@@ -209,11 +220,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       const uint32_t st = base + s * C::STAGE_BYTES;
       mbar_expect_tx(full_bar(s), C::STAGE_BYTES);
       const int x = kt * BK;
-      tma_load_2d(st, &maps.a_hi, x, m0, full_bar(s));
-      tma_load_2d(st + C::A_BYTES, &maps.a_lo, x, m0, full_bar(s));
-      tma_load_2d(st + 2 * C::A_BYTES, &maps.b_hi, x, n0, full_bar(s));
-      tma_load_2d(st + 2 * C::A_BYTES + C::B_BYTES, &maps.b_lo, x, n0, full_bar(s));
-      last_round[s] = kt / C::STAGES;
+#pragma unroll
+      for (int i = 0; i < S; ++i) tma_load_2d(st + i * C::A_BYTES, &maps.a[i], x, m0, full_bar(s));
+#pragma unroll
+      for (int j = 0; j < S; ++j) tma_load_2d(st + S * C::A_BYTES + j * C::B_BYTES, &maps.b[j], x, n0, full_bar(s));
+      last_round[s] = it / C::STAGES;
     }
     if (*abort_flag) {  // let issued copies land before the CTA's shared memory goes away
       for (int s = 0; s < C::STAGES; ++s)
@@ -222,9 +233,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
     bool ok = true;
-    for (int kt = 0; kt < num_k_tiles; ++kt) {
-      const int s = kt % C::STAGES;
-      const uint32_t ph = (uint32_t)(kt / C::STAGES) & 1u;
+    for (int it = 0; it < nk; ++it) {
+      const int s = it % C::STAGES;
+      const uint32_t ph = (uint32_t)(it / C::STAGES) & 1u;
       if (!mbar_wait(full_bar(s), ph, abort_flag)) {
         *abort_flag = 1;
         status_set(p.status, KF_ERR_TIMEOUT, p.step, 2);
@@ -233,15 +244,20 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t st = base + s * C::STAGE_BYTES;
-      const uint32_t a_hi = st, a_lo = st + C::A_BYTES;
-      const uint32_t b_hi = st + 2 * C::A_BYTES, b_lo = b_hi + C::B_BYTES;
 #pragma unroll
       for (int k = 0; k < BK / UMMA_K; ++k) {
         const uint32_t off = k * UMMA_K * 2;  // bytes along K inside the swizzle atom
-        const uint32_t acc = (kt > 0 || k > 0) ? 1u : 0u;
-        mma_bf16(tmem, smem_desc(a_hi + off), smem_desc(b_hi + off), C::IDESC, acc);
-        mma_bf16(tmem, smem_desc(a_hi + off), smem_desc(b_lo + off), C::IDESC, 1u);
-        mma_bf16(tmem, smem_desc(a_lo + off), smem_desc(b_hi + off), C::IDESC, 1u);
+        // products of slice levels i + j < S, least significant first
+#pragma unroll
+        for (int lvl = S - 1; lvl >= 0; --lvl) {
+#pragma unroll
+          for (int i = 0; i <= lvl; ++i) {
+            const int j = lvl - i;
+            const uint32_t acc = (it > 0 || k > 0 || lvl != S - 1 || i != 0) ? 1u : 0u;
+            mma_bf16(tmem, smem_desc(st + i * C::A_BYTES + off), smem_desc(st + S * C::A_BYTES + j * C::B_BYTES + off),
+                     C::IDESC, acc);
+          }
+        }
       }
       mma_commit(empty_bar(s));
     }
@@ -250,7 +266,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   } else if (warp >= 2) {
     // ---------------- epilogue: warp w reads TMEM lanes 32*(w%4) .. +31
     const int lane_base = 32 * (warp % 4);
-    bool ready = num_k_tiles > 0 ? mbar_wait(accum_bar, 0, abort_flag) : true;
+    bool ready = nk > 0 ? mbar_wait(accum_bar, 0, abort_flag) : true;
     if (!ready && !*abort_flag) {
       *abort_flag = 1;
       status_set(p.status, KF_ERR_TIMEOUT, p.step, 3);
@@ -261,7 +277,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 #pragma unroll 1
       for (int c = 0; c < BN; c += 32) {
         uint32_t r[32];
-        if (num_k_tiles > 0) {
+        if (nk > 0) {
           tmem_ld32(tmem + ((uint32_t)lane_base << 16) + (uint32_t)c, r);
         } else {
 #pragma unroll
@@ -327,38 +343,37 @@ kf_status make_map(CUtensorMap* map, const void* ptr, int64_t rows, int64_t cols
   return r == CUDA_SUCCESS ? KF_OK : KF_ERR_CUDA;
 }
 
-template <int BN>
-kf_status launch(cudaStream_t s, const GemmParams<float>& g, const __nv_bfloat16* a_hi, const __nv_bfloat16* a_lo,
-                 const __nv_bfloat16* b_hi, const __nv_bfloat16* b_lo, int64_t ldk) {
-  using C = TcCfg<BN>;
+template <int BN, int S>
+kf_status launch(cudaStream_t s, const GemmParams<float>& g, const TcScratch& sc, int64_t ldk) {
+  using C = TcCfg<BN, S>;
   TcMaps maps;
-  KF_TRY(make_map(&maps.a_hi, a_hi, g.M, ldk, ldk, BM));
-  KF_TRY(make_map(&maps.a_lo, a_lo, g.M, ldk, ldk, BM));
-  KF_TRY(make_map(&maps.b_hi, b_hi, g.N, ldk, ldk, BN));
-  KF_TRY(make_map(&maps.b_lo, b_lo, g.N, ldk, ldk, BN));
+  for (int i = 0; i < S; ++i) {
+    KF_TRY(make_map(&maps.a[i], sc.a[i], g.M, ldk, ldk, BM));
+    KF_TRY(make_map(&maps.b[i], sc.b[i], g.N, ldk, ldk, BN));
+  }
   static bool configured = false;
   if (!configured) {
-    KF_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
+    KF_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<BN, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
     configured = true;
   }
   dim3 grid((unsigned)ceil_div(g.N, BN), (unsigned)ceil_div(g.M, BM));
   const int num_k_tiles = (int)(ldk / BK);
-  tc_gemm_kernel<BN><<<grid, NUM_THREADS, C::SMEM, s>>>(maps, g, num_k_tiles);
+  tc_gemm_kernel<BN, S><<<grid, NUM_THREADS, C::SMEM, s>>>(maps, g, num_k_tiles);
   ++g_launches;
   return launch_check("tc_gemm");
 }
 
 }  // namespace
 
-uint64_t tc_scratch_bytes(int64_t rows, int64_t ld) { return 4ull * rows * ld * sizeof(__nv_bfloat16); }
+uint64_t tc_scratch_bytes(int64_t rows, int64_t ld) { return 6ull * rows * ld * sizeof(__nv_bfloat16); }
 
 kf_status tc_scratch_alloc(TcScratch& sc, int64_t rows, int64_t ld,
                            const std::function<kf_status(void**, size_t)>& alloc) {
   size_t plane = (size_t)rows * ld * sizeof(__nv_bfloat16);
-  KF_TRY(alloc((void**)&sc.a_hi, plane));
-  KF_TRY(alloc((void**)&sc.a_lo, plane));
-  KF_TRY(alloc((void**)&sc.b_hi, plane));
-  KF_TRY(alloc((void**)&sc.b_lo, plane));
+  for (int i = 0; i < 3; ++i) {
+    KF_TRY(alloc((void**)&sc.a[i], plane));
+    KF_TRY(alloc((void**)&sc.b[i], plane));
+  }
   sc.rows = rows;
   sc.ld = ld;
   return KF_OK;
@@ -378,21 +393,27 @@ bool tc_available() {
   return major == 10 && minor == 3 && encode_fn() != nullptr;
 }
 
-kf_status tc_gemm_bf16x3(cudaStream_t s, TcScratch& sc, const GemmParams<float>& g) {
+kf_status tc_gemm_split(cudaStream_t s, TcScratch& sc, const GemmParams<float>& g, int slices, bool transB) {
   if (g.M <= 0 || g.N <= 0) return KF_OK;
   if (g.sym && g.M != g.N) return KF_ERR_ARG;
-  const int64_t ldk = round_up(g.K > 0 ? g.K : 1, BK);
+  if (slices != 2 && slices != 3) return KF_ERR_ARG;
+  if (g.K == 0) {  // epilogue only: no operand tiles to load
+    GemmParams<float> h = g;
+    h.transA = 0;
+    return gemm_simt<float>(s, true, h);
+  }
+  const int64_t ldk = round_up(g.K, BK);
   if (g.M > sc.rows || g.N > sc.rows || ldk > sc.ld) return KF_ERR_ARG;
-  if (g.K > 0) {
-    KF_TRY(split_bf16(s, g.M, g.K, g.A, g.lda, sc.a_hi, sc.a_lo, ldk));
-    KF_TRY(split_bf16(s, g.N, g.K, g.B, g.ldb, sc.b_hi, sc.b_lo, ldk));
-  }
-  GemmParams<float> h = g;
-  if (g.K == 0) {
-    // epilogue-only product: no operand tiles to load
-    return gemm_simt<float>(s, true, g);
-  }
-  return launch<256>(s, h, sc.a_hi, sc.a_lo, sc.b_hi, sc.b_lo, ldk);
+  if (g.transA)
+    KF_TRY(split_bf16_t(s, g.M, g.K, g.A, g.lda, sc.a, slices, ldk));
+  else
+    KF_TRY(split_bf16(s, g.M, g.K, g.A, g.lda, sc.a, slices, ldk));
+  if (transB)
+    KF_TRY(split_bf16(s, g.N, g.K, g.B, g.ldb, sc.b, slices, ldk));
+  else
+    KF_TRY(split_bf16_t(s, g.N, g.K, g.B, g.ldb, sc.b, slices, ldk));
+  if (slices == 2) return launch<256, 2>(s, g, sc, ldk);
+  return launch<128, 3>(s, g, sc, ldk);
 }
 
 }  // namespace kfm

@@ -7,9 +7,10 @@
 
 namespace kfm {
 
-// Per-plan scratch: bf16 hi/lo planes of the two operands of one product.
+// Per-plan scratch: up to three bf16 planes of each operand of one product.
 struct TcScratch {
-  __nv_bfloat16 *a_hi = nullptr, *a_lo = nullptr, *b_hi = nullptr, *b_lo = nullptr;
+  __nv_bfloat16* a[3] = {nullptr, nullptr, nullptr};
+  __nv_bfloat16* b[3] = {nullptr, nullptr, nullptr};
   int64_t rows = 0, ld = 0;  // capacity: rows x ld elements per plane
 };
 
@@ -20,9 +21,13 @@ kf_status tc_scratch_alloc(TcScratch& sc, int64_t rows, int64_t ld,
 // True when this build carries the tcgen05 kernels.
 bool tc_available();
 
-// C = A B^T with A: M x K, B: N x K float32 (row-major), computed as
-// hi(A) hi(B)^T + hi(A) lo(B)^T + lo(A) hi(B)^T on the tensor cores with
-// float32 accumulation, followed by the epilogue of GemmParams.
-kf_status tc_gemm_bf16x3(cudaStream_t s, TcScratch& sc, const GemmParams<float>& g);
+// C = op(A) op(B) for float32 operands: A is M x K (or K x M with g.transA),
+// B is N x K when transB (C = A B^T) or K x N otherwise.  Each operand is
+// split into `slices` bf16 planes (2 or 3), transposing on the way where
+// needed, and the products of slice levels i + j < slices are accumulated in
+// float32 on the tensor cores (3 products for 2 slices, 6 for 3), followed by
+// the epilogue of GemmParams.  g.tri_a / g.tri_b skip zero k-tiles of
+// triangular operands.
+kf_status tc_gemm_split(cudaStream_t s, TcScratch& sc, const GemmParams<float>& g, int slices, bool transB = true);
 
 }  // namespace kfm

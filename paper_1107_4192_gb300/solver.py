@@ -63,10 +63,10 @@ class Plan:
 
     def __init__(self, N, m, T, f_kind=B.KF_F_IDENTITY, f_nnz=0, prec=B.KF_PREC_FP64,
                  solve_prec=B.KF_SOLVE_FP64, q_kind=B.KF_COV_SCALAR, r_kind=B.KF_COV_SCALAR, joseph_every=0,
-                 mem_budget_bytes=0, checkpoint_every=0, stream=None):
+                 mem_budget_bytes=0, checkpoint_every=0, split_terms=0, stream=None):
         self.N, self.m, self.T = N, m, T
         self.desc = B.make_desc(N, m, T, f_kind, prec, solve_prec, q_kind, r_kind, joseph_every, f_nnz,
-                                mem_budget_bytes, checkpoint_every, stream)
+                                mem_budget_bytes, checkpoint_every, split_terms, stream)
         self.handle = B.kf_plan(self.desc)
 
     @classmethod
@@ -109,11 +109,11 @@ class Plan:
 
 
 def run(prob, prec=B.KF_PREC_FP64, solve_prec=B.KF_SOLVE_FP64, joseph_every=0, checkpoint_every=0,
-        t_full=-1, device="cuda"):
+        t_full=-1, split_terms=0, device="cuda"):
     """Filter + smoother for a synthetic problem; returns numpy outputs."""
     d = upload(prob, device)
     with Plan.for_inputs(d, prob.N, prob.m, prob.T, prec=prec, solve_prec=solve_prec, joseph_every=joseph_every,
-                         checkpoint_every=checkpoint_every) as plan:
+                         checkpoint_every=checkpoint_every, split_terms=split_terms) as plan:
         xf, df = plan.filter(d)
         xs, ds, Pf = plan.smooth(t_full=t_full)
         out = dict(x_filt=xf.cpu().numpy(), diagP_filt=df.cpu().numpy(), x_smooth=xs.cpu().numpy(),

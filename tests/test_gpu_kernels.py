@@ -188,3 +188,33 @@ def test_tc_bf16x3_symmetric(n, K):
     ref = A.astype(np.float64) @ Bm.astype(np.float64).T + S0
     low = np.tril(np.ones((n, n), bool))
     assert np.abs(got - ref)[low].max() <= 1e-4 * np.abs(ref).max()
+
+
+def _split3_ref(X):
+    t = torch.from_numpy(np.ascontiguousarray(X, np.float32))
+    out = []
+    for _ in range(3):
+        h = t.bfloat16().float()
+        out.append(h.double().numpy())
+        t = t - h
+    return out
+
+
+@pytest.mark.parametrize("transB", [1, 0])
+@pytest.mark.parametrize("M,N,K", [(128, 128, 64), (300, 257, 130), (70, 513, 384)])
+def test_tc_bf16x6_gemm(transB, M, N, K):
+    """Three-way split (six bf16 products): exact emulation, and float32-class accuracy."""
+    rng = np.random.default_rng(M + N + K + transB)
+    A = rng.standard_normal((M, K)).astype(np.float32)
+    Bm = (rng.standard_normal((N, K)) if transB else rng.standard_normal((K, N))).astype(np.float32)
+    Bnk = Bm if transB else Bm.T
+    a = _split3_ref(A)
+    b = _split3_ref(Bnk)
+    exact = sum(a[i] @ b[j].T for i in range(3) for j in range(3) if i + j < 3)
+    dC = torch.zeros(M, N, dtype=torch.float32, device="cuda")
+    B.kfx_gemm(3, transB, 0, M, N, K, 1.0, torch.from_numpy(A).cuda(), K, torch.from_numpy(np.ascontiguousarray(Bm)).cuda(),
+               K if transB else N, 0.0, dC, N)
+    got = dC.double().cpu().numpy()
+    assert np.abs(got - exact).max() <= 4e-6 * max(1.0, np.sqrt(K)) * np.abs(exact).max()
+    full = A.astype(np.float64) @ Bnk.astype(np.float64).T
+    assert np.linalg.norm(got - full) <= 2e-6 * np.linalg.norm(full)

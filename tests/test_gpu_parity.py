@@ -75,6 +75,19 @@ def test_mixed_bf16x3_paths(solve, mesh):
     check(out, run_oracle(prob), TOL_MEAN32, TOL_DIAG32)
 
 
+@pytest.mark.parametrize("N,m,T", [(129, 20, 4), (257, 70, 5), (600, 64, 4)])
+def test_mixed_ragged_sizes(N, m, T):
+    prob = synth.random_walk_problem(N, m, T, seed=N + m)
+    out = solver.run(prob, prec=B.KF_PREC_MIXED_BF16X3, solve_prec=B.KF_SOLVE_FP32, joseph_every=2)
+    check(out, run_oracle(prob), TOL_MEAN32, TOL_DIAG32)
+
+
+def test_mixed_six_term_smoother_products():
+    prob = synth.mesh_problem(324, 30, 12, seed=4)
+    out = solver.run(prob, prec=B.KF_PREC_MIXED_BF16X3, solve_prec=B.KF_SOLVE_FP32, joseph_every=4, split_terms=6)
+    check(out, run_oracle(prob), TOL_MEAN32, TOL_DIAG32)
+
+
 def test_joseph_every_k_fp64():
     prob = synth.random_dense_problem(130, 20, 10, seed=9)
     check(solver.run(prob, prec=B.KF_PREC_FP64, joseph_every=3), run_oracle(prob), TOL64, TOL64)
