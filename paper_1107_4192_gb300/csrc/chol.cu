@@ -16,78 +16,187 @@ template <> int potrf_block<double>() { return 64; }
 template <> int potrf_block<float>() { return 128; }
 
 // Factors the n x n (n <= NB) lower triangle at A in shared memory, writes L
-// back (lower triangle only) and L^{-1} to dinv (NB x NB, zero above the diagonal).
+// back (lower triangle only) and L^{-1} to dinv (leading dimension ldd, zero
+// above the diagonal).  The block is padded to NB with an identity, so the
+// algorithm always runs on NB = 32 * P rows:
+//   for each 32-wide panel: one warp factors the 32 x 32 diagonal block in
+//   registers (shuffles, no block barrier) and inverts it; the rows below are
+//   solved against that inverse; the trailing lower triangle gets a rank-32
+//   update with register-blocked threads.
+// The inverse is then assembled by block forward substitution,
+//   X_pq = -X_pp sum_{r=q}^{p-1} L_pr X_rq.
+template <typename T, int NB>
+struct DiagSmem {
+  static constexpr int LD = NB + 1;
+  static constexpr int NP = NB / 32;
+  static constexpr int TSZ = NP * 32 * 33;
+  static constexpr size_t bytes = (2ull * NB * LD + TSZ) * sizeof(T);
+};
+
+template <typename T, int BS>
+__device__ __forceinline__ void trailing_update(T* S, int LD, int j0, int r0, int tx, int ty) {
+  // S[i][k] -= sum_c S[i][j0+c] S[k][j0+c] for i, k >= r0, k <= i; thread block (ty, tx) of BS x BS
+  T acc[BS][BS];
+#pragma unroll
+  for (int a = 0; a < BS; ++a)
+#pragma unroll
+    for (int b = 0; b < BS; ++b) acc[a][b] = T(0);
+  const int i0 = r0 + ty * BS, k0 = r0 + tx * BS;
+  if (k0 > i0 + BS - 1) return;  // block entirely above the diagonal
+#pragma unroll 4
+  for (int c = 0; c < 32; ++c) {
+    T li[BS], lk[BS];
+#pragma unroll
+    for (int a = 0; a < BS; ++a) li[a] = S[(i0 + a) * LD + j0 + c];
+#pragma unroll
+    for (int b = 0; b < BS; ++b) lk[b] = S[(k0 + b) * LD + j0 + c];
+#pragma unroll
+    for (int a = 0; a < BS; ++a)
+#pragma unroll
+      for (int b = 0; b < BS; ++b) acc[a][b] = fma(li[a], lk[b], acc[a][b]);
+  }
+#pragma unroll
+  for (int a = 0; a < BS; ++a)
+#pragma unroll
+    for (int b = 0; b < BS; ++b)
+      if (k0 + b <= i0 + a) S[(i0 + a) * LD + k0 + b] -= acc[a][b];
+}
+
 template <typename T, int NB>
 __global__ void __launch_bounds__(256) potrf_diag_kernel(T* A, int64_t lda, int n, T* dinv, int64_t ldd,
                                                          int* status, int step, int base) {
+  using Cfg = DiagSmem<T, NB>;
+  constexpr int LD = Cfg::LD;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int LD = NB + 1;
   T* S = reinterpret_cast<T*>(smem_raw);
   T* X = S + NB * LD;
+  T* Tb = X + NB * LD;
   __shared__ int fail;
   const int tid = threadIdx.x, nt = blockDim.x;
+  const int warp = tid / 32, lane = tid % 32;
   if (tid == 0) fail = status_failed(status) ? 1 : 0;  // one read for the whole CTA
   __syncthreads();
   if (fail) return;
 
-  for (int idx = tid; idx < n * n; idx += nt) {
-    int i = idx / n, j = idx % n;
-    S[i * LD + j] = (j <= i) ? A[(int64_t)i * lda + j] : T(0);
+  for (int idx = tid; idx < NB * NB; idx += nt) {
+    const int i = idx / NB, j = idx % NB;
+    T v = T(0);
+    if (i < n && j < n) {
+      if (j <= i) v = A[(int64_t)i * lda + j];
+    } else if (i == j) {
+      v = T(1);
+    }
+    S[i * LD + j] = v;
+    X[i * LD + j] = T(0);
   }
   __syncthreads();
 
-  for (int j = 0; j < n; ++j) {
-    if (tid == 0) {
-      T d = S[j * LD + j];
-      if (!(d > T(0)) || !isfinite((double)d)) {
-        fail = 1;
-        status_set(status, KF_ERR_NOT_PD, step, base + j);
+  for (int p = 0; p < Cfg::NP; ++p) {
+    const int j0 = p * 32;
+    // (a) one warp: factor and invert the 32 x 32 diagonal block
+    if (warp == 0) {
+      T a[32];
+#pragma unroll
+      for (int k = 0; k < 32; ++k) a[k] = k <= lane ? S[(j0 + lane) * LD + j0 + k] : T(0);
+      int bad = -1;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const T d = __shfl_sync(0xffffffffu, a[j], j);
+        if (bad < 0 && !(d > T(0) && isfinite((double)d))) bad = j;
+        const T ljj = Num<T>::sqrt_(d);
+        const T inv = T(1) / ljj;
+        if (lane == j) a[j] = ljj;
+        else if (lane > j) a[j] *= inv;
+        const T cj = a[j];
+#pragma unroll
+        for (int k = j + 1; k < 32; ++k) {
+          const T lk = __shfl_sync(0xffffffffu, cj, k);
+          if (lane >= k) a[k] -= cj * lk;
+        }
+      }
+      if (bad >= 0) {
+        if (lane == 0) {
+          fail = 1;
+          status_set(status, KF_ERR_NOT_PD, step, base + j0 + bad);
+        }
       } else {
-        S[j * LD + j] = Num<T>::sqrt_(d);
+#pragma unroll
+        for (int k = 0; k < 32; ++k)
+          if (k <= lane) S[(j0 + lane) * LD + j0 + k] = a[k];
+        __syncwarp();
+        // column `lane` of the block inverse: x_i = (delta_{i,lane} - sum_{k<i} L_ik x_k) / L_ii
+        T x[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          T acc = (i == lane) ? T(1) : T(0);
+#pragma unroll
+          for (int k = 0; k < i; ++k) acc -= S[(j0 + i) * LD + j0 + k] * x[k];
+          x[i] = acc / S[(j0 + i) * LD + j0 + i];
+        }
+#pragma unroll
+        for (int i = 0; i < 32; ++i) X[(j0 + i) * LD + j0 + lane] = x[i];
       }
     }
     __syncthreads();
     if (fail) return;
-    const T ljj = S[j * LD + j];
-    for (int i = j + 1 + tid; i < n; i += nt) S[i * LD + j] /= ljj;
-    __syncthreads();
-    const int r = n - j - 1;
-    for (int idx = tid; idx < r * r; idx += nt) {
-      int ii = idx / r, kk = idx % r;
-      if (kk <= ii) {
-        int i = j + 1 + ii, k = j + 1 + kk;
-        S[i * LD + k] -= S[i * LD + j] * S[k * LD + j];
+    const int r0 = j0 + 32, R = NB - r0;
+    if (R <= 0) break;
+    // (b) panel below: L[i][j0+c] = sum_{k<=c} A[i][j0+k] X[j0+c][j0+k], staged through Tb
+    for (int item = tid; item < R * 8; item += nt) {
+      const int i = r0 + item / 8, c0 = (item % 8) * 4;
+      T o[4] = {T(0), T(0), T(0), T(0)};
+      for (int k = 0; k < 32; ++k) {
+        const T av = S[i * LD + j0 + k];
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) o[cc] = fma(av, X[(j0 + c0 + cc) * LD + j0 + k], o[cc]);
       }
+#pragma unroll
+      for (int cc = 0; cc < 4; ++cc) Tb[(item / 8) * 33 + c0 + cc] = o[cc];
+    }
+    __syncthreads();
+    for (int idx = tid; idx < R * 32; idx += nt) S[(r0 + idx / 32) * LD + j0 + idx % 32] = Tb[(idx / 32) * 33 + idx % 32];
+    __syncthreads();
+    // (c) trailing rank-32 update of the lower triangle, 16 x 16 threads
+    {
+      const int tx = tid % 16, ty = tid / 16;
+      if (R == 96) trailing_update<T, 6>(S, LD, j0, r0, tx, ty);
+      else if (R == 64) trailing_update<T, 4>(S, LD, j0, r0, tx, ty);
+      else if (R == 32) trailing_update<T, 2>(S, LD, j0, r0, tx, ty);
+    }
+    __syncthreads();
+  }
+
+  // (d) assemble the inverse: X_pq = -X_pp sum_{r=q}^{p-1} L_pr X_rq
+  for (int p = 1; p < Cfg::NP; ++p) {
+    for (int item = tid; item < p * 32 * 8; item += nt) {
+      const int q = item / 256, rr = (item % 256) / 8, c0 = (item % 8) * 4;
+      T o[4] = {T(0), T(0), T(0), T(0)};
+      for (int k = 32 * q; k < 32 * p; ++k) {
+        const T lv = S[(32 * p + rr) * LD + k];
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) o[cc] = fma(lv, X[k * LD + 32 * q + c0 + cc], o[cc]);
+      }
+#pragma unroll
+      for (int cc = 0; cc < 4; ++cc) Tb[(q * 32 + rr) * 33 + c0 + cc] = o[cc];
+    }
+    __syncthreads();
+    for (int item = tid; item < p * 32 * 8; item += nt) {
+      const int q = item / 256, rr = (item % 256) / 8, c0 = (item % 8) * 4;
+      T o[4] = {T(0), T(0), T(0), T(0)};
+      for (int k = 0; k <= rr; ++k) {
+        const T xv = X[(32 * p + rr) * LD + 32 * p + k];
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) o[cc] = fma(xv, Tb[(q * 32 + k) * 33 + c0 + cc], o[cc]);
+      }
+#pragma unroll
+      for (int cc = 0; cc < 4; ++cc) X[(32 * p + rr) * LD + 32 * q + c0 + cc] = -o[cc];
     }
     __syncthreads();
   }
 
   for (int idx = tid; idx < n * n; idx += nt) {
-    int i = idx / n, j = idx % n;
+    const int i = idx / n, j = idx % n;
     if (j <= i) A[(int64_t)i * lda + j] = S[i * LD + j];
-  }
-
-  // X = L^{-1}: thread c owns column c and walks down it (no barrier needed,
-  // X[k][c] for k < i was produced by the same thread).
-  for (int c = tid; c < NB; c += nt) {
-    if (c < n) {
-      for (int i = 0; i < c; ++i) X[i * LD + c] = T(0);
-      X[c * LD + c] = T(1) / S[c * LD + c];
-      for (int i = c + 1; i < n; ++i) {
-        T a0 = T(0), a1 = T(0);
-        int k = c;
-        for (; k + 1 < i; k += 2) {
-          a0 = fma(S[i * LD + k], X[k * LD + c], a0);
-          a1 = fma(S[i * LD + k + 1], X[(k + 1) * LD + c], a1);
-        }
-        if (k < i) a0 = fma(S[i * LD + k], X[k * LD + c], a0);
-        X[i * LD + c] = -(a0 + a1) / S[i * LD + i];
-      }
-    }
-  }
-  __syncthreads();
-  for (int idx = tid; idx < n * n; idx += nt) {
-    int i = idx / n, j = idx % n;
     dinv[(int64_t)i * ldd + j] = j <= i ? X[i * LD + j] : T(0);
   }
 }
@@ -95,11 +204,11 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(T* A, int64_t lda, int 
 template <typename T, int NB>
 static kf_status launch_potrf_diag(cudaStream_t s, T* A, int64_t lda, int n, T* dinv, int64_t ldd, int* status,
                                    int step, int base) {
-  const size_t smem = 2ull * NB * (NB + 1) * sizeof(T);
+  const size_t smem = DiagSmem<T, NB>::bytes;
   static bool configured = false;
   if (!configured) {
-    cudaFuncSetAttribute(potrf_diag_kernel<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
+    KF_CUDA_TRY(cudaFuncSetAttribute(potrf_diag_kernel<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
     configured = true;
   }
   potrf_diag_kernel<T, NB><<<1, 256, smem, s>>>(A, lda, n, dinv, ldd, status, step, base);
@@ -110,6 +219,7 @@ static kf_status launch_potrf_diag(cudaStream_t s, T* A, int64_t lda, int n, T* 
 template <typename T>
 kf_status potrf_diag(cudaStream_t s, T* A, int64_t lda, int n, T* dinv, int64_t ldd, int* status, int step,
                      int base) {
+  if (n <= 32) return launch_potrf_diag<T, 32>(s, A, lda, n, dinv, ldd, status, step, base);
   if (n <= 64) return launch_potrf_diag<T, 64>(s, A, lda, n, dinv, ldd, status, step, base);
   if (sizeof(T) == 8 || n > 128) return KF_ERR_ARG;
   return launch_potrf_diag<T, 128>(s, A, lda, n, dinv, ldd, status, step, base);
