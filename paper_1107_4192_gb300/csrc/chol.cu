@@ -78,16 +78,17 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(T* A, int64_t lda, int 
   __syncthreads();
   if (fail) return;
 
-  for (int idx = tid; idx < NB * NB; idx += nt) {
-    const int i = idx / NB, j = idx % NB;
-    T v = T(0);
-    if (i < n && j < n) {
-      if (j <= i) v = A[(int64_t)i * lda + j];
-    } else if (i == j) {
-      v = T(1);
+  for (int i = tid / 32; i < NB; i += nt / 32) {
+    for (int j = tid % 32; j < NB; j += 32) {
+      T v = T(0);
+      if (i < n && j < n) {
+        if (j <= i) v = A[(int64_t)i * lda + j];
+      } else if (i == j) {
+        v = T(1);
+      }
+      S[i * LD + j] = v;
+      X[i * LD + j] = T(0);
     }
-    S[i * LD + j] = v;
-    X[i * LD + j] = T(0);
   }
   __syncthreads();
 
@@ -95,7 +96,8 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(T* A, int64_t lda, int 
     const int j0 = p * 32;
     // (a) one warp: factor and invert the 32 x 32 diagonal block
     if (warp == 0) {
-      T a[32];
+      // lane i holds row i of the block (a[k], k <= i)
+      T a[32], rinv[32];
 #pragma unroll
       for (int k = 0; k < 32; ++k) a[k] = k <= lane ? S[(j0 + lane) * LD + j0 + k] : T(0);
       int bad = -1;
@@ -105,6 +107,7 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(T* A, int64_t lda, int 
         if (bad < 0 && !(d > T(0) && isfinite((double)d))) bad = j;
         const T ljj = Num<T>::sqrt_(d);
         const T inv = T(1) / ljj;
+        rinv[j] = inv;
         if (lane == j) a[j] = ljj;
         else if (lane > j) a[j] *= inv;
         const T cj = a[j];
@@ -120,19 +123,23 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(T* A, int64_t lda, int 
           status_set(status, KF_ERR_NOT_PD, step, base + j0 + bad);
         }
       } else {
-#pragma unroll
-        for (int k = 0; k < 32; ++k)
-          if (k <= lane) S[(j0 + lane) * LD + j0 + k] = a[k];
-        __syncwarp();
-        // column `lane` of the block inverse: x_i = (delta_{i,lane} - sum_{k<i} L_ik x_k) / L_ii
+        // column `lane` of the block inverse: x_i = (delta_{i,lane} - sum_{k<i} L_ik x_k) / L_ii,
+        // with L_ik broadcast from lane i
         T x[32];
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
-          T acc = (i == lane) ? T(1) : T(0);
+          T acc0 = (i == lane) ? T(1) : T(0), acc1 = T(0);
 #pragma unroll
-          for (int k = 0; k < i; ++k) acc -= S[(j0 + i) * LD + j0 + k] * x[k];
-          x[i] = acc / S[(j0 + i) * LD + j0 + i];
+          for (int k = 0; k < i; ++k) {
+            const T lik = __shfl_sync(0xffffffffu, a[k], i);
+            if (k & 1) acc1 -= lik * x[k];
+            else acc0 -= lik * x[k];
+          }
+          x[i] = (acc0 + acc1) * rinv[i];
         }
+#pragma unroll
+        for (int k = 0; k < 32; ++k)
+          if (k <= lane) S[(j0 + lane) * LD + j0 + k] = a[k];
 #pragma unroll
         for (int i = 0; i < 32; ++i) X[(j0 + i) * LD + j0 + lane] = x[i];
       }
@@ -194,10 +201,11 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(T* A, int64_t lda, int 
     __syncthreads();
   }
 
-  for (int idx = tid; idx < n * n; idx += nt) {
-    const int i = idx / n, j = idx % n;
-    if (j <= i) A[(int64_t)i * lda + j] = S[i * LD + j];
-    dinv[(int64_t)i * ldd + j] = j <= i ? X[i * LD + j] : T(0);
+  for (int i = tid / 32; i < n; i += nt / 32) {
+    for (int j = tid % 32; j < n; j += 32) {
+      if (j <= i) A[(int64_t)i * lda + j] = S[i * LD + j];
+      dinv[(int64_t)i * ldd + j] = j <= i ? X[i * LD + j] : T(0);
+    }
   }
 }
 

@@ -133,6 +133,17 @@ kf_status spmm_pft(cudaStream_t s, int64_t N, const int64_t* rowptr, const int64
 kf_status split_bf16(cudaStream_t s, int64_t rows, int64_t cols, const float* A, int64_t lda,
                      __nv_bfloat16* const* planes, int n, int64_t ldh);
 
+// Splits the two operands of one product in a single launch: for op = A, B,
+// planes (rows x ldh) of src (rows x cols) or of its transpose when trans
+// (src is then cols x rows).
+struct SplitOp {
+  const float* src = nullptr;
+  int64_t ld = 0, rows = 0, cols = 0;
+  int trans = 0;
+  __nv_bfloat16* planes[3] = {nullptr, nullptr, nullptr};
+};
+kf_status split_bf16_pair(cudaStream_t s, const SplitOp& a, const SplitOp& b, int n, int64_t ldh);
+
 // As split_bf16 for the transpose: plane[r][k] = split(A[k][r]) for r < rows,
 // k < cols, where A is cols x rows with leading dimension lda.
 kf_status split_bf16_t(cudaStream_t s, int64_t rows, int64_t cols, const float* A, int64_t lda,

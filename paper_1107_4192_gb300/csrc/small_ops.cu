@@ -275,6 +275,48 @@ kf_status split_bf16_t(cudaStream_t s, int64_t rows, int64_t cols, const float* 
   return launch_check("split_bf16_t");
 }
 
+// One 32 x 32 output tile of the planes per CTA; blockIdx.z picks the operand.
+__global__ void split_bf16_pair_kernel(SplitOp a, SplitOp b, int n, int64_t ldh) {
+  __shared__ float tile[32][33];
+  const SplitOp& op = blockIdx.z == 0 ? a : b;
+  const int64_t r0 = (int64_t)blockIdx.x * 32, k0 = (int64_t)blockIdx.y * 32;
+  if (r0 >= op.rows || k0 >= ldh) return;
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;  // 32 x 8 threads
+  if (op.trans) {
+    for (int i = ty; i < 32; i += 8) {
+      const int64_t k = k0 + i, r = r0 + tx;
+      tile[i][tx] = (k < op.cols && r < op.rows) ? op.src[k * op.ld + r] : 0.0f;
+    }
+  } else {
+    for (int i = ty; i < 32; i += 8) {
+      const int64_t r = r0 + i, k = k0 + tx;
+      tile[tx][i] = (k < op.cols && r < op.rows) ? op.src[r * op.ld + k] : 0.0f;
+    }
+  }
+  __syncthreads();
+  for (int i = ty; i < 32; i += 8) {
+    const int64_t r = r0 + i, k = k0 + tx;
+    if (r >= op.rows || k >= ldh) continue;
+    float v = tile[tx][i];
+    for (int s = 0; s < n; ++s) {
+      __nv_bfloat16 h = __float2bfloat16_rn(v);
+      op.planes[s][r * ldh + k] = h;
+      v -= __bfloat162float(h);
+    }
+  }
+}
+
+kf_status split_bf16_pair(cudaStream_t s, const SplitOp& a, const SplitOp& b, int n, int64_t ldh) {
+  if (n < 1 || n > 3) return KF_ERR_ARG;
+  const int64_t rows = std::max(a.rows, b.rows);
+  if (rows <= 0) return KF_OK;
+  if (ceil_div(rows, 32) > 0x7fffffff || ceil_div(ldh, 32) > 65535) return KF_ERR_ARG;
+  dim3 grid((unsigned)ceil_div(rows, 32), (unsigned)ceil_div(ldh, 32), 2);
+  split_bf16_pair_kernel<<<grid, 256, 0, s>>>(a, b, n, ldh);
+  ++g_launches;
+  return launch_check("split_bf16_pair");
+}
+
 template <typename T>
 __global__ void diag_kernel(int64_t n, const T* A, int64_t lda, double* d) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)

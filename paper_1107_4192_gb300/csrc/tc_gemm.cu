@@ -404,14 +404,14 @@ kf_status tc_gemm_split(cudaStream_t s, TcScratch& sc, const GemmParams<float>& 
   }
   const int64_t ldk = round_up(g.K, BK);
   if (g.M > sc.rows || g.N > sc.rows || ldk > sc.ld) return KF_ERR_ARG;
-  if (g.transA)
-    KF_TRY(split_bf16_t(s, g.M, g.K, g.A, g.lda, sc.a, slices, ldk));
-  else
-    KF_TRY(split_bf16(s, g.M, g.K, g.A, g.lda, sc.a, slices, ldk));
-  if (transB)
-    KF_TRY(split_bf16(s, g.N, g.K, g.B, g.ldb, sc.b, slices, ldk));
-  else
-    KF_TRY(split_bf16_t(s, g.N, g.K, g.B, g.ldb, sc.b, slices, ldk));
+  SplitOp oa, ob;
+  oa.src = g.A; oa.ld = g.lda; oa.rows = g.M; oa.cols = g.K; oa.trans = g.transA;
+  ob.src = g.B; ob.ld = g.ldb; ob.rows = g.N; ob.cols = g.K; ob.trans = transB ? 0 : 1;
+  for (int i = 0; i < slices; ++i) {
+    oa.planes[i] = sc.a[i];
+    ob.planes[i] = sc.b[i];
+  }
+  KF_TRY(split_bf16_pair(s, oa, ob, slices, ldk));
   if (slices == 2) return launch<256, 2>(s, g, sc, ldk);
   return launch<128, 3>(s, g, sc, ldk);
 }
