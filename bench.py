@@ -238,7 +238,7 @@ def main():
         dist.barrier()
     elapsed = ev0.elapsed_time(ev1) / 1e3
     launches = B.kf_plan_launch_count(plan.handle) - launches0
-    prof = {c: B.kf_plan_profile_read(plan.handle, c) for c in range(5)}
+    prof = {c: B.kf_plan_profile_read(plan.handle, c) for c in range(7)}
     B.kf_plan_profile(plan.handle, False)
     if world > 1:
         t = torch.tensor([elapsed], device="cuda", dtype=torch.float64)
@@ -273,8 +273,9 @@ def main():
     peaks, peak_src = load_peaks()
 
     # dominant kernel class by device time inside the timed region
-    names = {0: "filter_update", 1: "innovation", 2: "smoother_gemm", 3: "smoother_solve", 4: "predict"}
-    dom = max(prof, key=lambda c: prof[c][1])
+    names = {0: "filter_update", 1: "innovation", 2: "smoother_gemm", 3: "smoother_solve", 4: "predict",
+             5: "solve_factor", 6: "solve_gain"}
+    dom = max((c for c in prof if c < 5), key=lambda c: prof[c][1])
     n_l, ms_l = prof[dom]
     avg_s = ms_l / 1e3 / max(n_l, 1)
     if dom == 2:

@@ -173,7 +173,10 @@ typedef enum {
   KF_KC_SMOOTH_GEMM = 2,     /* W = J D and P_{t|T} = P_{t|t} + W J^T              */
   KF_KC_SMOOTH_SOLVE = 3,    /* Cholesky of P_{t+1|t} and the two solves           */
   KF_KC_PREDICT = 4,         /* F P F^T + Q                                        */
-  KF_KC_COUNT = 5
+  KF_KC_SOLVE_FACTOR = 5,    /* inside SMOOTH_SOLVE: Cholesky (+ inverse) of       */
+                             /* P_{t+1|t}                                          */
+  KF_KC_SOLVE_GAIN = 6,      /* inside SMOOTH_SOLVE: forming J_t from the factor   */
+  KF_KC_COUNT = 7
 } kf_kernel_class;
 kf_status kf_plan_profile(kf_plan_t p, int32_t enable);
 kf_status kf_plan_profile_read(kf_plan_t p, int32_t cls, int64_t* launches,

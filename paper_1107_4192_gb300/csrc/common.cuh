@@ -14,8 +14,9 @@ namespace kfm {
 
 // Device status word layout: [0] = kf_status code of the first failure,
 // [1] = 1-based time step of the failure, [2] = index inside the failing
-// factorisation (pivot) or element, [3] = spare.
-enum { ST_CODE = 0, ST_STEP = 1, ST_INDEX = 2, ST_WORDS = 4 };
+// factorisation (pivot) or element, [3] = current step for kernels launched
+// with step < 0 (replayed CUDA graphs, whose arguments are fixed).
+enum { ST_CODE = 0, ST_STEP = 1, ST_INDEX = 2, ST_CUR = 3, ST_WORDS = 4 };
 
 __device__ __forceinline__ bool status_failed(const int* st) {
   return st != nullptr && *(volatile const int*)st != 0;
@@ -24,7 +25,7 @@ __device__ __forceinline__ bool status_failed(const int* st) {
 __device__ __forceinline__ void status_set(int* st, int code, int step, int index) {
   if (st == nullptr) return;
   if (atomicCAS(st + ST_CODE, 0, code) == 0) {
-    st[ST_STEP] = step;
+    st[ST_STEP] = step < 0 ? st[ST_CUR] : step;
     st[ST_INDEX] = index;
   }
 }

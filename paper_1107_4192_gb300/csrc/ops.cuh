@@ -97,6 +97,9 @@ template <typename T>
 kf_status gemv(cudaStream_t s, int64_t rows, int64_t cols, const T* A, int64_t lda,
                const double* x, const double* ybase, double sign, double* y);
 
+// status[ST_CUR] = step (read by graph-replayed kernels that report failures)
+kf_status set_status_step(cudaStream_t s, int* status, int step);
+
 // d[i] = a[i] - b[i]
 kf_status vsub(cudaStream_t s, int64_t n, const double* a, const double* b, double* d);
 

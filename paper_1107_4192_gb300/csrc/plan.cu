@@ -58,6 +58,12 @@ struct kf_plan_s {
   char *Sl = nullptr, *Sldinv = nullptr;
   char *Lb = nullptr, *Ldinv = nullptr, *Jb = nullptr;
   float* Wi = nullptr;    // L^{-1} for the tensor-core solve (mixed mode, float32 solve)
+  // The Cholesky + inverse of P_{t+1|t} is the same launch sequence at every
+  // smoother step (only the step number differs, which kernels read from the
+  // status word), so it is captured once into a CUDA graph and replayed.
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t chol_graph = nullptr;
+  int64_t graph_launches = 0;  // kernels inside one replay of chol_graph
   char *Jm = nullptr, *Wb = nullptr, *Db = nullptr, *Pn = nullptr;
   TcScratch tc{};
   double *F = nullptr, *Q = nullptr, *H = nullptr, *R = nullptr;
@@ -396,6 +402,46 @@ kf_status run_filter(kf_plan_s* p, const double* Y, const double* x0, const doub
   return read_status(p, fail_step);
 }
 
+// Cholesky + inverse of the working P_{t+1|t} (in Lb) for smoother step `step`,
+// replayed from a CUDA graph after the first step has run eagerly.
+kf_status chol_inverse_step(kf_plan_s* p, float* Lb, int step) {
+  const int N = (int)p->N;
+  if (!p->chol_graph && p->cap_stream == nullptr) {
+    // first use: run eagerly (also configures every kernel), then capture
+    KF_TRY(chol_inverse_tc(p->s, p->tc, N, Lb, p->ldN, p->Wi, p->ldN, (float*)p->tmpN, p->ldN, p->status, step));
+    if (cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      p->cap_stream = nullptr;
+      return KF_OK;
+    }
+    const int64_t l0 = g_launches;
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      return KF_OK;
+    }
+    kf_status st = chol_inverse_tc(p->cap_stream, p->tc, N, Lb, p->ldN, p->Wi, p->ldN, (float*)p->tmpN, p->ldN,
+                                   p->status, -1);
+    cudaError_t e = cudaStreamEndCapture(p->cap_stream, &graph);
+    if (st == KF_OK && e == cudaSuccess && graph &&
+        cudaGraphInstantiate(&p->chol_graph, graph, 0) == cudaSuccess) {
+      p->graph_launches = g_launches - l0;
+    } else {
+      p->chol_graph = nullptr;
+    }
+    g_launches = l0;
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return KF_OK;
+  }
+  if (!p->chol_graph)
+    return chol_inverse_tc(p->s, p->tc, N, Lb, p->ldN, p->Wi, p->ldN, (float*)p->tmpN, p->ldN, p->status, step);
+  KF_TRY(set_status_step(p->s, p->status, step));
+  KF_CUDA_TRY(cudaGraphLaunch(p->chol_graph, p->s));
+  g_launches += p->graph_launches;
+  return KF_OK;
+}
+
 template <typename B, typename V>
 kf_status run_smoother(kf_plan_s* p, double* x_smooth, double* diagP_smooth, double* P_full, int64_t t_full,
                        int64_t* fail_step) {
@@ -437,11 +483,13 @@ kf_status run_smoother(kf_plan_s* p, double* x_smooth, double* diagP_smooth, dou
       // P_{t+1|t} = L L^T
       KF_TRY((copy2d<V, B>(s, Lb, ldN, Pn, ldN, N, N)));
       const bool tc_solve = p->bulk == BULK_BF16X3 && sizeof(V) == 4;
-      if (tc_solve)
-        KF_TRY(chol_inverse_tc(s, p->tc, (int)N, (float*)Lb, ldN, p->Wi, ldN, (float*)p->tmpN, ldN, p->status,
-                               (int)(t + 1)));
-      else
-        KF_TRY(potrf<V>(s, Lb, ldN, (int)N, (V*)p->Ldinv, nbs, p->status, (int)(t + 1)));
+      {
+        Prof pf(p, KF_KC_SOLVE_FACTOR);
+        if (tc_solve)
+          KF_TRY(chol_inverse_step(p, (float*)Lb, (int)(t + 1)));
+        else
+          KF_TRY(potrf<V>(s, Lb, ldN, (int)N, (V*)p->Ldinv, nbs, p->status, (int)(t + 1)));
+      }
       KF_TRY(get_P<B>(p, t, &Pt));
       // J_t = P_{t|t} F^T P_{t+1|t}^{-1}
       const B* Bm = Pt;
@@ -458,6 +506,7 @@ kf_status run_smoother(kf_plan_s* p, double* x_smooth, double* diagP_smooth, dou
         KF_TRY(gemm_simt<B>(s, true, f));
         Bm = (const B*)p->tmpN;
       }
+      Prof pg(p, KF_KC_SOLVE_GAIN);
       if (tc_solve) {
         if (Bm != Pt) {  // Bm lives in tmpN, which the products below use as scratch
           KF_TRY((copy2d<B, B>(s, (B*)Jb, ldN, Bm, ldN, N, N)));
@@ -760,6 +809,8 @@ int64_t kf_plan_launch_count(kf_plan_t p) { return p ? g_launches - p->launches0
 void kf_plan_destroy(kf_plan_t p) {
   if (!p) return;
   if (p->s) cudaStreamSynchronize(p->s);
+  if (p->chol_graph) cudaGraphExecDestroy(p->chol_graph);
+  if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   for (void* a : p->allocs) cudaFree(a);
   for (auto& mk : p->marks) {
     cudaEventDestroy(mk.a);

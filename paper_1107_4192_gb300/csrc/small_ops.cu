@@ -76,6 +76,14 @@ kf_status gemv(cudaStream_t s, int64_t rows, int64_t cols, const T* A, int64_t l
   return launch_check("gemv");
 }
 
+__global__ void set_step_kernel(int* status, int step) { status[ST_CUR] = step; }
+
+kf_status set_status_step(cudaStream_t s, int* status, int step) {
+  set_step_kernel<<<1, 1, 0, s>>>(status, step);
+  ++g_launches;
+  return launch_check("set_step");
+}
+
 __global__ void vsub_kernel(int64_t n, const double* a, const double* b, double* d) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     d[i] = a[i] - b[i];
