@@ -63,7 +63,7 @@ __device__ __forceinline__ void trailing_update(T* S, int LD, int j0, int r0, in
 }
 
 template <typename T, int NB>
-__global__ void __launch_bounds__(256) potrf_diag_kernel(T* A, int64_t lda, int n, T* dinv, int64_t ldd,
+__global__ void __launch_bounds__(256, 1) potrf_diag_kernel(T* A, int64_t lda, int n, T* dinv, int64_t ldd,
                                                          int* status, int step, int base) {
   using Cfg = DiagSmem<T, NB>;
   constexpr int LD = Cfg::LD;
@@ -97,24 +97,22 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(T* A, int64_t lda, int 
     // (a) one warp: factor and invert the 32 x 32 diagonal block
     if (warp == 0) {
       // lane i holds row i of the block (a[k], k <= i)
-      T a[32], rinv[32];
+      T a[32];
 #pragma unroll
       for (int k = 0; k < 32; ++k) a[k] = k <= lane ? S[(j0 + lane) * LD + j0 + k] : T(0);
       int bad = -1;
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
         const T d = __shfl_sync(0xffffffffu, a[j], j);
-        if (bad < 0 && !(d > T(0) && isfinite((double)d))) bad = j;
+        if (bad < 0 && !(d > T(0) && d < T(INFINITY))) bad = j;
         const T ljj = Num<T>::sqrt_(d);
-        const T inv = T(1) / ljj;
-        rinv[j] = inv;
         if (lane == j) a[j] = ljj;
-        else if (lane > j) a[j] *= inv;
+        else if (lane > j) a[j] = a[j] / ljj;
         const T cj = a[j];
 #pragma unroll
         for (int k = j + 1; k < 32; ++k) {
           const T lk = __shfl_sync(0xffffffffu, cj, k);
-          if (lane >= k) a[k] -= cj * lk;
+          if (lane >= k) a[k] = fma(-cj, lk, a[k]);
         }
       }
       if (bad >= 0) {
@@ -123,8 +121,9 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(T* A, int64_t lda, int 
           status_set(status, KF_ERR_NOT_PD, step, base + j0 + bad);
         }
       } else {
+        const T my_inv = T(1) / a[lane < 32 ? lane : 0];  // 1 / L_ii of this lane's row
         // column `lane` of the block inverse: x_i = (delta_{i,lane} - sum_{k<i} L_ik x_k) / L_ii,
-        // with L_ik broadcast from lane i
+        // with L_ik and 1 / L_ii broadcast from lane i
         T x[32];
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
@@ -132,10 +131,10 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(T* A, int64_t lda, int 
 #pragma unroll
           for (int k = 0; k < i; ++k) {
             const T lik = __shfl_sync(0xffffffffu, a[k], i);
-            if (k & 1) acc1 -= lik * x[k];
-            else acc0 -= lik * x[k];
+            if (k & 1) acc1 = fma(-lik, x[k], acc1);
+            else acc0 = fma(-lik, x[k], acc0);
           }
-          x[i] = (acc0 + acc1) * rinv[i];
+          x[i] = (acc0 + acc1) * __shfl_sync(0xffffffffu, my_inv, i);
         }
 #pragma unroll
         for (int k = 0; k < 32; ++k)
@@ -152,6 +151,7 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(T* A, int64_t lda, int 
     for (int item = tid; item < R * 8; item += nt) {
       const int i = r0 + item / 8, c0 = (item % 8) * 4;
       T o[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
       for (int k = 0; k < 32; ++k) {
         const T av = S[i * LD + j0 + k];
 #pragma unroll
@@ -178,10 +178,14 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(T* A, int64_t lda, int 
     for (int item = tid; item < p * 32 * 8; item += nt) {
       const int q = item / 256, rr = (item % 256) / 8, c0 = (item % 8) * 4;
       T o[4] = {T(0), T(0), T(0), T(0)};
-      for (int k = 32 * q; k < 32 * p; ++k) {
-        const T lv = S[(32 * p + rr) * LD + k];
+      for (int kb = 32 * q; kb < 32 * p; kb += 32) {
 #pragma unroll
-        for (int cc = 0; cc < 4; ++cc) o[cc] = fma(lv, X[k * LD + 32 * q + c0 + cc], o[cc]);
+        for (int kk = 0; kk < 32; ++kk) {
+          const int k = kb + kk;
+          const T lv = S[(32 * p + rr) * LD + k];
+#pragma unroll
+          for (int cc = 0; cc < 4; ++cc) o[cc] = fma(lv, X[k * LD + 32 * q + c0 + cc], o[cc]);
+        }
       }
 #pragma unroll
       for (int cc = 0; cc < 4; ++cc) Tb[(q * 32 + rr) * 33 + c0 + cc] = o[cc];
@@ -190,7 +194,8 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(T* A, int64_t lda, int 
     for (int item = tid; item < p * 32 * 8; item += nt) {
       const int q = item / 256, rr = (item % 256) / 8, c0 = (item % 8) * 4;
       T o[4] = {T(0), T(0), T(0), T(0)};
-      for (int k = 0; k <= rr; ++k) {
+#pragma unroll
+      for (int k = 0; k < 32; ++k) {  // X_pp is zero above its diagonal
         const T xv = X[(32 * p + rr) * LD + 32 * p + k];
 #pragma unroll
         for (int cc = 0; cc < 4; ++cc) o[cc] = fma(xv, Tb[(q * 32 + k) * 33 + c0 + cc], o[cc]);
