@@ -43,7 +43,7 @@ __device__ __forceinline__ void trailing_update(T* S, int LD, int j0, int r0, in
     for (int b = 0; b < BS; ++b) acc[a][b] = T(0);
   const int i0 = r0 + ty * BS, k0 = r0 + tx * BS;
   if (k0 > i0 + BS - 1) return;  // block entirely above the diagonal
-#pragma unroll 4
+#pragma unroll 2
   for (int c = 0; c < 32; ++c) {
     T li[BS], lk[BS];
 #pragma unroll
@@ -96,7 +96,10 @@ __global__ void __launch_bounds__(256, 1) potrf_diag_kernel(T* A, int64_t lda, i
     const int j0 = p * 32;
     // (a) one warp: factor and invert the 32 x 32 diagonal block
     if (warp == 0) {
-      // lane i holds row i of the block (a[k], k <= i)
+      // Lane i holds row i of the 32 x 32 block in registers.  Step j scales
+      // column j, publishes it in shared memory (Tb) and every lane applies the
+      // rank-1 update to its row from broadcast loads, which are independent
+      // of each other and so overlap.
       T a[32];
 #pragma unroll
       for (int k = 0; k < 32; ++k) a[k] = k <= lane ? S[(j0 + lane) * LD + j0 + k] : T(0);
@@ -106,14 +109,17 @@ __global__ void __launch_bounds__(256, 1) potrf_diag_kernel(T* A, int64_t lda, i
         const T d = __shfl_sync(0xffffffffu, a[j], j);
         if (bad < 0 && !(d > T(0) && d < T(INFINITY))) bad = j;
         const T ljj = Num<T>::sqrt_(d);
+        if (lane > j) a[j] = a[j] / ljj;
         if (lane == j) a[j] = ljj;
-        else if (lane > j) a[j] = a[j] / ljj;
-        const T cj = a[j];
+        Tb[lane] = a[j];
+        __syncwarp();
+        const T lij = a[j];
 #pragma unroll
         for (int k = j + 1; k < 32; ++k) {
-          const T lk = __shfl_sync(0xffffffffu, cj, k);
-          if (lane >= k) a[k] = fma(-cj, lk, a[k]);
+          const T lk = Tb[k];
+          if (lane >= k) a[k] = fma(-lij, lk, a[k]);
         }
+        __syncwarp();
       }
       if (bad >= 0) {
         if (lane == 0) {
@@ -121,24 +127,27 @@ __global__ void __launch_bounds__(256, 1) potrf_diag_kernel(T* A, int64_t lda, i
           status_set(status, KF_ERR_NOT_PD, step, base + j0 + bad);
         }
       } else {
-        const T my_inv = T(1) / a[lane < 32 ? lane : 0];  // 1 / L_ii of this lane's row
-        // column `lane` of the block inverse: x_i = (delta_{i,lane} - sum_{k<i} L_ik x_k) / L_ii,
-        // with L_ik and 1 / L_ii broadcast from lane i
-        T x[32];
-#pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          T acc0 = (i == lane) ? T(1) : T(0), acc1 = T(0);
-#pragma unroll
-          for (int k = 0; k < i; ++k) {
-            const T lik = __shfl_sync(0xffffffffu, a[k], i);
-            if (k & 1) acc1 = fma(-lik, x[k], acc1);
-            else acc0 = fma(-lik, x[k], acc0);
-          }
-          x[i] = (acc0 + acc1) * __shfl_sync(0xffffffffu, my_inv, i);
-        }
 #pragma unroll
         for (int k = 0; k < 32; ++k)
           if (k <= lane) S[(j0 + lane) * LD + j0 + k] = a[k];
+        __syncwarp();
+        // lane c computes column c of the block inverse, x_i = (delta_ic - sum_{k<i} L_ik x_k) / L_ii,
+        // with L_ik broadcast from shared memory
+        const T* P = S + j0 * LD + j0;
+        T x[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          T acc0 = (i == lane) ? T(1) : T(0), acc1 = T(0), acc2 = T(0), acc3 = T(0);
+#pragma unroll
+          for (int k = 0; k < i; ++k) {
+            const T lik = P[i * LD + k];
+            if ((k & 3) == 0) acc0 = fma(-lik, x[k], acc0);
+            else if ((k & 3) == 1) acc1 = fma(-lik, x[k], acc1);
+            else if ((k & 3) == 2) acc2 = fma(-lik, x[k], acc2);
+            else acc3 = fma(-lik, x[k], acc3);
+          }
+          x[i] = ((acc0 + acc1) + (acc2 + acc3)) / P[i * LD + i];
+        }
 #pragma unroll
         for (int i = 0; i < 32; ++i) X[(j0 + i) * LD + j0 + lane] = x[i];
       }
@@ -151,7 +160,7 @@ __global__ void __launch_bounds__(256, 1) potrf_diag_kernel(T* A, int64_t lda, i
     for (int item = tid; item < R * 8; item += nt) {
       const int i = r0 + item / 8, c0 = (item % 8) * 4;
       T o[4] = {T(0), T(0), T(0), T(0)};
-#pragma unroll
+#pragma unroll 4
       for (int k = 0; k < 32; ++k) {
         const T av = S[i * LD + j0 + k];
 #pragma unroll
@@ -179,7 +188,7 @@ __global__ void __launch_bounds__(256, 1) potrf_diag_kernel(T* A, int64_t lda, i
       const int q = item / 256, rr = (item % 256) / 8, c0 = (item % 8) * 4;
       T o[4] = {T(0), T(0), T(0), T(0)};
       for (int kb = 32 * q; kb < 32 * p; kb += 32) {
-#pragma unroll
+#pragma unroll 4
         for (int kk = 0; kk < 32; ++kk) {
           const int k = kb + kk;
           const T lv = S[(32 * p + rr) * LD + k];
@@ -194,7 +203,7 @@ __global__ void __launch_bounds__(256, 1) potrf_diag_kernel(T* A, int64_t lda, i
     for (int item = tid; item < p * 32 * 8; item += nt) {
       const int q = item / 256, rr = (item % 256) / 8, c0 = (item % 8) * 4;
       T o[4] = {T(0), T(0), T(0), T(0)};
-#pragma unroll
+#pragma unroll 4
       for (int k = 0; k < 32; ++k) {  // X_pp is zero above its diagonal
         const T xv = X[(32 * p + rr) * LD + 32 * p + k];
 #pragma unroll

@@ -52,7 +52,7 @@ struct kf_plan_s {
   char* store = nullptr;
   char* seg = nullptr;
   double *xpred = nullptr, *xfilt = nullptr, *xs = nullptr, *nu = nullptr, *dx = nullptr;
-  char *P = nullptr, *Ut = nullptr, *KV = nullptr, *VK = nullptr, *Hb = nullptr, *tmpN = nullptr;
+  char *P = nullptr, *Ut = nullptr, *Zb = nullptr, *KV = nullptr, *VK = nullptr, *Hb = nullptr, *tmpN = nullptr;
   char *Fb = nullptr, *S0b = nullptr;
   double *S = nullptr, *S0 = nullptr, *Sdinv = nullptr, *partials = nullptr;
   char *Sl = nullptr, *Sldinv = nullptr;
@@ -108,7 +108,7 @@ Sizes sizes_for(const kf_desc* d) {
   z.slot = N * ldN * z.b;
   uint64_t w = 0;
   w += 2 * z.slot;                          // P, tmpN
-  w += N * ldm * z.b;                       // Ut
+  w += 2 * N * ldm * z.b;                   // Ut, Z
   w += 2 * N * 2 * ldm * z.b;               // KV, VK
   w += m * ldN * z.b;                       // Hb
   w += 2 * m * m * 8 + round_up(m, 64) * 64 * 8 + kSplitsS * m * m * 8;  // S, S0, Sdinv, partials
@@ -305,19 +305,24 @@ kf_status filter_step(kf_plan_s* p, int64_t t, const double* y, double* diag_out
     L = (const B*)p->Sl;
     Ld = (const B*)p->Sldinv;
   }
-  // K = U^T S^{-1} = U^T L^{-T} L^{-1}, in the left half of KV
-  KF_TRY((copy2d<B, B>(s, KV, ldkv, Ut, ldm, N, m)));
-  KF_TRY(trsm_right<B>(s, true, N, m, L, m, Ld, nbS, KV, ldkv, p->status));
-  KF_TRY(trsm_right<B>(s, false, N, m, L, m, Ld, nbS, KV, ldkv, p->status));
+  // Square-root form of the gain: with S = L L^T, Z = U^T L^{-T} (N x m), so that
+  // K = Z L^{-1}, K U = Z Z^T and K nu = Z (L^{-1} nu).  Z needs one triangular
+  // solve and is conditioned like L (the square root of cond(S)); the m-sized
+  // solve L^{-1} nu of the mean update runs in float64.
+  B* Z = (B*)p->Zb;
+  KF_TRY((copy2d<B, B>(s, Z, ldm, Ut, ldm, N, m)));
+  KF_TRY(trsm_right<B>(s, true, N, m, L, m, Ld, nbS, Z, ldm, p->status));
   if (y) {
     KF_TRY(innovation(s, m, N, p->H, p->xpred + t * N, y, p->nu, p->status, (int)t));
-    KF_TRY(gemv<B>(s, N, m, KV, ldkv, p->nu, p->xpred + t * N, 1.0, p->xfilt + t * N));
+    // nu <- L^{-1} nu  (as the 1 x m row solve nu^T L^{-T}), float64
+    KF_TRY(trsm_right<double>(s, true, 1, m, p->S, m, p->Sdinv, nbS, p->nu, m, p->status));
+    KF_TRY(gemv<B>(s, N, m, Z, ldm, p->nu, p->xpred + t * N, 1.0, p->xfilt + t * N));
   }
   const bool ident = p->d.f_kind == KF_F_IDENTITY;
   B* dst = (B*)p->slot_ptr(t);
-  GemmParams<B> u;  // P_{t|t} = P - K U  (symmetric by construction), P <- P_{t|t} + Q when F = I
+  GemmParams<B> u;  // P_{t|t} = P - Z Z^T  (symmetric by construction), P <- P_{t|t} + Q when F = I
   u.M = N; u.N = N;
-  u.A = KV; u.lda = ldkv;
+  u.A = Z; u.lda = ldm;
   u.alpha = B(-1);
   u.cin = P; u.ldcin = ldN; u.beta = B(1);
   u.out = dst; u.ldo = ldN;
@@ -332,7 +337,9 @@ kf_status filter_step(kf_plan_s* p, int64_t t, const double* y, double* diag_out
   u.sym = 1;
   if (joseph) {
     // Joseph form (I - KH) P (I - KH)^T + K R K^T = P - K V^T - V K^T with
-    // V = U^T - K S / 2: one rank-2m product [K V][V K]^T.
+    // K = Z L^{-1} and V = U^T - K S / 2: one rank-2m product [K V][V K]^T.
+    KF_TRY((copy2d<B, B>(s, KV, ldkv, Z, ldm, N, m)));
+    KF_TRY(trsm_right<B>(s, false, N, m, L, m, Ld, nbS, KV, ldkv, p->status));
     KF_TRY((copy2d<B, double>(s, (B*)p->S0b, m, p->S0, m, m, m)));
     GemmParams<B> v;
     v.M = N; v.N = m; v.K = m;
@@ -346,11 +353,12 @@ kf_status filter_step(kf_plan_s* p, int64_t t, const double* y, double* diag_out
     B* VK = (B*)p->VK;
     KF_TRY((copy2d<B, B>(s, VK, ldkv, KV + ldm, ldkv, N, m)));
     KF_TRY((copy2d<B, B>(s, VK + ldm, ldkv, KV, ldkv, N, m)));
+    u.A = KV; u.lda = ldkv;
     u.K = (int)ldkv;
     u.B = VK; u.ldb = ldkv;
   } else {
     u.K = p->bulk == BULK_BF16X3 ? (int)ldm : m;
-    u.B = Ut; u.ldb = ldm;
+    u.B = Z; u.ldb = ldm;
   }
   {
     Prof pr(p, KF_KC_FILTER_UPDATE);
@@ -644,6 +652,7 @@ kf_status kf_plan(kf_plan_t* out, const kf_desc* d) {
   A(&p->P, p->slot);
   A(&p->tmpN, p->slot);
   A(&p->Ut, N * ldm * b);
+  A(&p->Zb, N * ldm * b);
   A(&p->KV, N * 2 * ldm * b);
   A(&p->VK, N * 2 * ldm * b);
   A(&p->Hb, m * ldN * b);
