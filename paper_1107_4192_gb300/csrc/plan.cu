@@ -58,6 +58,7 @@ struct kf_plan_s {
   char *Sl = nullptr, *Sldinv = nullptr;
   char *Lb = nullptr, *Ldinv = nullptr, *Jb = nullptr;
   float* Wi = nullptr;    // L^{-1} for the tensor-core solve (mixed mode, float32 solve)
+  double *P64 = nullptr, *W64 = nullptr, *U64 = nullptr, *Z64 = nullptr;  // float64 first update
   // The Cholesky + inverse of P_{t+1|t} is the same launch sequence at every
   // smoother step (only the step number differs, which kernels read from the
   // status word), so it is captured once into a CUDA graph and replayed.
@@ -81,9 +82,13 @@ struct kf_plan_s {
   std::vector<cudaEvent_t> pool;
   int64_t launches0 = 0;
 
+  // Store slots: every P_{t|t} when ckpt == 1; otherwise checkpoints at
+  // t = 0, c, 2c, .., a permanent slot for t = 1 (see filter_first_fp64) and a
+  // segment buffer for the other steps of one segment.
   char* slot_ptr(int64_t t) {
     if (ckpt == 1) return store + (size_t)t * slot;
     if (t % ckpt == 0) return store + (size_t)(t / ckpt) * slot;
+    if (t == 1) return store + (size_t)nck * slot;
     return seg + (size_t)(t % ckpt - 1) * slot;
   }
 };
@@ -117,6 +122,7 @@ Sizes sizes_for(const kf_desc* d) {
   w += 2 * N * ldN * z.sb + round_up(N, nbs) * nbs * z.sb;                 // Lb, Jb, Ldinv
   w += (z.sb != z.b ? z.slot : 0) + 3 * z.slot;                            // Jm, Wb, Db, Pn
   if (d->prec == KF_PREC_MIXED_BF16X3 && z.sb == 4) w += z.slot;         // Wi
+  if (z.b == 4) w += N * ldN * 8 * (d->f_kind != KF_F_IDENTITY ? 2 : 1) + 2 * N * ldm * 8;  // first update
   w += 3 * (T + 1) * N * 8 + m * 8 + N * 8;                                // means
   if (d->f_kind == KF_F_CSR) w += d->f_nnz * 16 + (N + 1) * 8;
   if (d->f_kind == KF_F_DENSE) w += N * N * 8 + z.slot;
@@ -145,7 +151,7 @@ kf_status choose_checkpoint(const kf_desc* d, const Sizes& z, int64_t* c_out, ui
   const int64_t T = d->T;
   auto store_bytes = [&](int64_t c) -> uint64_t {
     if (c <= 1) return (uint64_t)(T + 1) * z.slot;
-    return (uint64_t)(T / c + 1 + c - 1) * z.slot;
+    return (uint64_t)(T / c + 1 + 1 + c - 1) * z.slot;
   };
   if (d->checkpoint_every > 0) {
     int64_t c = d->checkpoint_every > T ? T : d->checkpoint_every;
@@ -368,9 +374,76 @@ kf_status filter_step(kf_plan_s* p, int64_t t, const double* y, double* diag_out
   return KF_OK;
 }
 
+// The first update in float64 for the float32 stores.  P0 is usually far
+// above the posterior in the directions the sensors see (by 1 + lambda(H P0
+// H^T) / r), so P_{1|1} = P_{1|0} - Z Z^T cancels most of its leading digits
+// there; in float32 that cancellation leaves errors of order 1e-4 relative in
+// the small eigenvalues, which the next steps carry.  From t = 2 on the
+// prior is already close to the posterior and float32 is enough.  P_{1|1} is
+// rounded to float32 only after the subtraction.
+kf_status filter_first_fp64(kf_plan_s* p, const double* P0, const double* y, double* diag_out) {
+  cudaStream_t s = p->s;
+  const int N = (int)p->N, m = (int)p->m;
+  const int64_t ldN = p->ldN, ldm = p->ldm;
+  double* P = p->P64;
+  if (p->d.f_kind == KF_F_IDENTITY) {
+    KF_TRY((add_cov<double, double>(s, P, ldN, P0, N, N, p->d.q_kind, p->Q)));
+  } else if (p->d.f_kind == KF_F_CSR) {
+    KF_TRY(spmm_fpft<double>(s, N, p->Frp, p->Fcol, p->F, P0, N, p->W64, ldN, P, ldN, p->d.q_kind, p->Q));
+  } else {
+    GemmParams<double> g;  // W = F P0, then P = W F^T + Q
+    g.M = N; g.N = N; g.K = N;
+    g.A = p->F; g.lda = N;
+    g.B = P0; g.ldb = N;
+    g.out = p->W64; g.ldo = ldN;
+    KF_TRY(gemm_simt<double>(s, false, g));
+    GemmParams<double> h;
+    h.M = N; h.N = N; h.K = N;
+    h.A = p->W64; h.lda = ldN;
+    h.B = p->F; h.ldb = N;
+    h.out2 = P; h.ldo2 = ldN;
+    h.q_kind = p->d.q_kind; h.q = p->Q; h.ldq = N;
+    KF_TRY(gemm_simt<double>(s, true, h));
+  }
+  GemmParams<double> g;  // U^T = P H^T
+  g.M = N; g.N = m; g.K = N;
+  g.A = P; g.lda = ldN;
+  g.B = p->H; g.ldb = N;
+  g.out = p->U64; g.ldo = ldm;
+  g.status = p->status;
+  KF_TRY(gemm_simt<double>(s, true, g));
+  KF_TRY(innovation_cov<double>(s, m, N, p->H, N, p->U64, ldm, p->d.r_kind, p->R, p->S, m, p->partials, kSplitsS));
+  const int nbS = potrf_block<double>();
+  KF_TRY(potrf<double>(s, p->S, m, m, p->Sdinv, nbS, p->status, 1));
+  KF_TRY((copy2d<double, double>(s, p->Z64, ldm, p->U64, ldm, N, m)));
+  KF_TRY(trsm_right<double>(s, true, N, m, p->S, m, p->Sdinv, nbS, p->Z64, ldm, p->status));
+  KF_TRY(innovation(s, m, N, p->H, p->xpred + N, y, p->nu, p->status, 1));
+  KF_TRY(trsm_right<double>(s, true, 1, m, p->S, m, p->Sdinv, nbS, p->nu, m, p->status));
+  KF_TRY(gemv<double>(s, N, m, p->Z64, ldm, p->nu, p->xpred + N, 1.0, p->xfilt + N));
+  GemmParams<double> u;  // P_{1|1} = P_{1|0} - Z Z^T
+  u.M = N; u.N = N; u.K = m;
+  u.A = p->Z64; u.lda = ldm;
+  u.B = p->Z64; u.ldb = ldm;
+  u.alpha = -1.0;
+  u.cin = P; u.ldcin = ldN; u.beta = 1.0;
+  u.out = P; u.ldo = ldN;
+  u.diag_out = diag_out;
+  u.check_diag = 1;
+  u.step = 1;
+  u.status = p->status;
+  u.sym = 1;
+  KF_TRY(gemm_simt<double>(s, true, u));
+  float* dst = (float*)p->slot_ptr(1);
+  KF_TRY((copy2d<float, double>(s, dst, ldN, P, ldN, N, N)));
+  if (p->d.f_kind == KF_F_IDENTITY) return add_cov<float, double>(s, (float*)p->P, ldN, P, ldN, N, p->d.q_kind, p->Q);
+  return predict_cov<float>(p, dst, (float*)p->P);
+}
+
 template <typename B>
 kf_status recompute_segment(kf_plan_s* p, int64_t k) {
-  const int64_t c = p->ckpt, t0 = k * c, t1 = std::min<int64_t>(t0 + c - 1, p->T);
+  const int64_t c = p->ckpt, t1 = std::min<int64_t>(k * c + c - 1, p->T);
+  // segment 0 restarts from the kept P_{1|1}, the others from their checkpoint
+  const int64_t t0 = k == 0 ? 1 : k * c;
   KF_TRY(predict_cov<B>(p, (const B*)p->slot_ptr(t0), (B*)p->P));
   for (int64_t t = t0 + 1; t <= t1; ++t) KF_TRY(filter_step<B>(p, t, nullptr, nullptr));
   p->seg_id = k;
@@ -379,7 +452,8 @@ kf_status recompute_segment(kf_plan_s* p, int64_t k) {
 
 template <typename B>
 kf_status get_P(kf_plan_s* p, int64_t t, const B** out) {
-  if (p->ckpt > 1 && t % p->ckpt != 0 && p->seg_id != t / p->ckpt) KF_TRY(recompute_segment<B>(p, t / p->ckpt));
+  if (p->ckpt > 1 && t % p->ckpt != 0 && t != 1 && p->seg_id != t / p->ckpt)
+    KF_TRY(recompute_segment<B>(p, t / p->ckpt));
   *out = (const B*)p->slot_ptr(t);
   return KF_OK;
 }
@@ -403,7 +477,11 @@ kf_status run_filter(kf_plan_s* p, const double* Y, const double* x0, const doub
   KF_TRY(predict_cov<B>(p, (const B*)p->slot_ptr(0), (B*)p->P));
   for (int64_t t = 1; t <= T; ++t) {
     KF_TRY(predict_mean(s, p->d.f_kind, N, p->F, p->Frp, p->Fcol, p->xfilt + (t - 1) * N, p->xpred + t * N));
-    KF_TRY(filter_step<B>(p, t, Y + (t - 1) * m, diagP_filt ? diagP_filt + (t - 1) * N : nullptr));
+    double* dg = diagP_filt ? diagP_filt + (t - 1) * N : nullptr;
+    if (t == 1 && sizeof(B) == 4)
+      KF_TRY(filter_first_fp64(p, P0, Y, dg));
+    else
+      KF_TRY(filter_step<B>(p, t, Y + (t - 1) * m, dg));
     if (p->ckpt > 1 && t % p->ckpt != 0) p->seg_id = t / p->ckpt;
   }
   KF_CUDA_TRY(cudaMemcpyAsync(x_filt, p->xfilt + N, (size_t)T * N * 8, cudaMemcpyDeviceToDevice, s));
@@ -641,7 +719,7 @@ kf_status kf_plan(kf_plan_t* out, const kf_desc* d) {
   auto A = [&](auto** ptr, size_t bytes) {
     if (st == KF_OK) st = dalloc(p, ptr, bytes);
   };
-  A(&p->store, store_bytes - (c > 1 ? (size_t)(c - 1) * p->slot : 0));
+  A(&p->store, store_bytes - (c > 1 ? (size_t)(c - 1) * p->slot : 0));  // checkpoints (+ the t = 1 slot)
   if (c > 1) A(&p->seg, (size_t)(c - 1) * p->slot);
   p->nck = c > 1 ? T / c + 1 : T + 1;
   A(&p->xpred, (T + 1) * N * 8);
@@ -669,6 +747,12 @@ kf_status kf_plan(kf_plan_t* out, const kf_desc* d) {
   A(&p->Ldinv, round_up(N, nbs) * nbs * sb);
   if (sb != b) A(&p->Jm, p->slot);
   if (p->bulk == BULK_BF16X3 && sb == 4) A(&p->Wi, p->slot);
+  if (b == 4) {
+    A(&p->P64, N * ldN * 8);
+    if (d->f_kind != KF_F_IDENTITY) A(&p->W64, N * ldN * 8);
+    A(&p->U64, N * ldm * 8);
+    A(&p->Z64, N * ldm * 8);
+  }
   A(&p->Wb, p->slot);
   A(&p->Db, p->slot);
   A(&p->Pn, p->slot);

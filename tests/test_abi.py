@@ -67,7 +67,7 @@ def test_footprint_and_checkpoint_policy(built_lib):
     d.mem_budget_bytes = w + 40 * 8196 * ldN * 4
     st, w2, s2, c2 = B.kf_plan_footprint(d)
     assert st == 0 and c2 > 1 and w2 + s2 <= d.mem_budget_bytes
-    assert s2 == (300 // c2 + 1 + c2 - 1) * 8196 * ldN * 4
+    assert s2 == (300 // c2 + 1 + 1 + c2 - 1) * 8196 * ldN * 4
     d.mem_budget_bytes = w + 5 * 8196 * ldN * 4
     st, *_ = B.kf_plan_footprint(d)
     assert st == B.KF_ERR_BUDGET
