@@ -24,6 +24,10 @@ __device__ __forceinline__ void epilogue_store(const GemmParams<T>& p, int gi, i
     p.out[(int64_t)gi * p.ldo + gj] = v;
     if (mirror) p.out[(int64_t)gj * p.ldo + gi] = v;
   }
+  if (p.outf) {
+    p.outf[(int64_t)gi * p.ldof + gj] = (float)v;
+    if (mirror) p.outf[(int64_t)gj * p.ldof + gi] = (float)v;
+  }
   if (p.out2) {
     T w = vpre + (T)q_value(p.q_kind, p.q, p.ldq, gi, gj);
     p.out2[(int64_t)gi * p.ldo2 + gj] = w;

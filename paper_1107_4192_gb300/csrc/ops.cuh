@@ -34,6 +34,8 @@ struct GemmParams {
   int64_t ldo = 0;
   T* out2 = nullptr;
   int64_t ldo2 = 0;
+  float* outf = nullptr;  // optional float32 copy of out (v), mirrored like out
+  int64_t ldof = 0;
   int q_kind = -1;
   const double* q = nullptr;
   int64_t ldq = 0;
@@ -140,9 +142,10 @@ kf_status split_bf16(cudaStream_t s, int64_t rows, int64_t cols, const float* A,
 // planes (rows x ldh) of src (rows x cols) or of its transpose when trans
 // (src is then cols x rows).
 struct SplitOp {
-  const float* src = nullptr;
+  const void* src = nullptr;  // float32, or float64 when f64
   int64_t ld = 0, rows = 0, cols = 0;
   int trans = 0;
+  int f64 = 0;
   __nv_bfloat16* planes[3] = {nullptr, nullptr, nullptr};
 };
 kf_status split_bf16_pair(cudaStream_t s, const SplitOp& a, const SplitOp& b, int n, int64_t ldh);

@@ -374,6 +374,116 @@ kf_status filter_step(kf_plan_s* p, int64_t t, const double* y, double* diag_out
   return KF_OK;
 }
 
+// F P F^T + Q for the float64 working covariance of the mixed mode, in place
+// (P -> P_{t+1|t}).  The mesh coupling runs in float64 on the CUDA cores
+// (HBM-bound); a dense F uses split-bf16 tensor-core products with a float64
+// epilogue.
+kf_status predict_cov64(kf_plan_s* p, double* P) {
+  Prof pr(p, KF_KC_PREDICT);
+  cudaStream_t s = p->s;
+  const int N = (int)p->N;
+  const int64_t ldN = p->ldN;
+  if (p->d.f_kind == KF_F_IDENTITY) return add_cov<double, double>(s, P, ldN, P, ldN, N, p->d.q_kind, p->Q);
+  if (p->d.f_kind == KF_F_CSR)
+    return spmm_fpft<double>(s, N, p->Frp, p->Fcol, p->F, P, ldN, p->W64, ldN, P, ldN, p->d.q_kind, p->Q);
+  GemmParams<double> w;  // W = F P
+  w.M = N; w.N = N; w.K = N;
+  w.out = p->W64; w.ldo = ldN;
+  w.status = p->status;
+  KF_TRY(tc_gemm_ops(s, p->tc, TcOperand{p->F, N, 1, 0}, TcOperand{P, ldN, 1, 1}, w, 3));
+  GemmParams<double> h;  // P = W F^T + Q
+  h.M = N; h.N = N; h.K = N;
+  h.out2 = P; h.ldo2 = ldN;
+  h.q_kind = p->d.q_kind; h.q = p->Q; h.ldq = N;
+  h.status = p->status;
+  return tc_gemm_ops(s, p->tc, TcOperand{p->W64, ldN, 1, 0}, TcOperand{p->F, N, 1, 0}, h, 3);
+}
+
+// One filter step of the mixed mode.  The working covariance P_{t|t-1} is
+// kept in float64 (p->P64): its well-observed directions have variances far
+// below its others, so float32 storage alone would limit the filter to about
+// 1e-4 relative accuracy at N ~ 10^4.  Products are three-way split-bf16 on
+// the tensor cores (float32-class), added to the float64 P in the epilogue;
+// P_{t|t} is rounded to float32 only for the smoother's store.
+kf_status filter_step_mixed(kf_plan_s* p, int64_t t, const double* y, double* diag_out) {
+  cudaStream_t s = p->s;
+  const int N = (int)p->N, m = (int)p->m;
+  const int64_t ldN = p->ldN, ldm = p->ldm, ldkv = 2 * p->ldm;
+  double* P = p->P64;
+  float* Ut = (float*)p->Ut;
+  {
+    Prof pr(p, KF_KC_INNOVATION);
+    GemmParams<float> g;  // U^T = P H^T
+    g.M = N; g.N = m; g.K = N;
+    g.out = Ut; g.ldo = ldm;
+    g.status = p->status;
+    KF_TRY(tc_gemm_ops(s, p->tc, TcOperand{P, ldN, 1, 0}, TcOperand{p->H, N, 1, 0}, g, 3));
+  }
+  KF_TRY(innovation_cov<float>(s, m, N, p->H, N, Ut, ldm, p->d.r_kind, p->R, p->S, m, p->partials, kSplitsS));
+  const bool joseph = p->d.joseph_every > 0 && (t % p->d.joseph_every) == 0;
+  if (joseph) KF_CUDA_TRY(cudaMemcpyAsync(p->S0, p->S, (size_t)m * m * 8, cudaMemcpyDeviceToDevice, s));
+  const int nbS = potrf_block<double>();
+  KF_TRY(potrf<double>(s, p->S, m, m, p->Sdinv, nbS, p->status, (int)t));
+  KF_TRY((copy2d<float, double>(s, (float*)p->Sl, m, p->S, m, m, m)));
+  KF_TRY((copy2d<float, double>(s, (float*)p->Sldinv, nbS, p->Sdinv, nbS, round_up(m, nbS), nbS)));
+  const float* L = (const float*)p->Sl;
+  const float* Ld = (const float*)p->Sldinv;
+  float* Z = (float*)p->Zb;  // Z = U^T L^{-T}
+  KF_TRY((copy2d<float, float>(s, Z, ldm, Ut, ldm, N, m)));
+  KF_TRY(trsm_right<float>(s, true, N, m, L, m, Ld, nbS, Z, ldm, p->status));
+  if (y) {
+    KF_TRY(innovation(s, m, N, p->H, p->xpred + t * N, y, p->nu, p->status, (int)t));
+    KF_TRY(trsm_right<double>(s, true, 1, m, p->S, m, p->Sdinv, nbS, p->nu, m, p->status));
+    KF_TRY(gemv<float>(s, N, m, Z, ldm, p->nu, p->xpred + t * N, 1.0, p->xfilt + t * N));
+  }
+  const bool ident = p->d.f_kind == KF_F_IDENTITY;
+  GemmParams<double> u;  // P_{t|t} = P - Z Z^T (float64 result, float32 copy to the store)
+  u.M = N; u.N = N;
+  u.alpha = -1.0;
+  u.cin = P; u.ldcin = ldN; u.beta = 1.0;
+  u.outf = (float*)p->slot_ptr(t); u.ldof = ldN;
+  if (ident) {
+    u.out2 = P; u.ldo2 = ldN;
+    u.q_kind = p->d.q_kind; u.q = p->Q; u.ldq = N;
+  } else {
+    u.out = P; u.ldo = ldN;
+  }
+  u.diag_out = diag_out;
+  u.check_diag = 1;
+  u.step = (int)t;
+  u.status = p->status;
+  u.sym = 1;
+  TcOperand ua{Z, ldm, 0, 0}, ub{Z, ldm, 0, 0};
+  u.K = (int)ldm;
+  if (joseph) {
+    float* KV = (float*)p->KV;
+    float* VK = (float*)p->VK;
+    KF_TRY((copy2d<float, float>(s, KV, ldkv, Z, ldm, N, m)));
+    KF_TRY(trsm_right<float>(s, false, N, m, L, m, Ld, nbS, KV, ldkv, p->status));
+    KF_TRY((copy2d<float, double>(s, (float*)p->S0b, m, p->S0, m, m, m)));
+    GemmParams<float> v;  // V = U^T - K S / 2
+    v.M = N; v.N = m; v.K = m;
+    v.A = KV; v.lda = ldkv;
+    v.B = (const float*)p->S0b; v.ldb = m;
+    v.alpha = -0.5f;
+    v.cin = Ut; v.ldcin = ldm; v.beta = 1.0f;
+    v.out = KV + ldm; v.ldo = ldkv;
+    v.status = p->status;
+    KF_TRY(gemm_simt<float>(s, true, v));
+    KF_TRY((copy2d<float, float>(s, VK, ldkv, KV + ldm, ldkv, N, m)));
+    KF_TRY((copy2d<float, float>(s, VK + ldm, ldkv, KV, ldkv, N, m)));
+    ua = TcOperand{KV, ldkv, 0, 0};
+    ub = TcOperand{VK, ldkv, 0, 0};
+    u.K = (int)ldkv;
+  }
+  {
+    Prof pr(p, KF_KC_FILTER_UPDATE);
+    KF_TRY(tc_gemm_ops(s, p->tc, ua, ub, u, 3));
+  }
+  if (!ident) KF_TRY(predict_cov64(p, P));
+  return KF_OK;
+}
+
 // The first update in float64 for the float32 stores.  P0 is usually far
 // above the posterior in the directions the sensors see (by 1 + lambda(H P0
 // H^T) / r), so P_{1|1} = P_{1|0} - Z Z^T cancels most of its leading digits
@@ -435,6 +545,7 @@ kf_status filter_first_fp64(kf_plan_s* p, const double* P0, const double* y, dou
   KF_TRY(gemm_simt<double>(s, true, u));
   float* dst = (float*)p->slot_ptr(1);
   KF_TRY((copy2d<float, double>(s, dst, ldN, P, ldN, N, N)));
+  if (p->bulk == BULK_BF16X3) return predict_cov64(p, P);  // the mixed filter continues in float64
   if (p->d.f_kind == KF_F_IDENTITY) return add_cov<float, double>(s, (float*)p->P, ldN, P, ldN, N, p->d.q_kind, p->Q);
   return predict_cov<float>(p, dst, (float*)p->P);
 }
@@ -444,6 +555,13 @@ kf_status recompute_segment(kf_plan_s* p, int64_t k) {
   const int64_t c = p->ckpt, t1 = std::min<int64_t>(k * c + c - 1, p->T);
   // segment 0 restarts from the kept P_{1|1}, the others from their checkpoint
   const int64_t t0 = k == 0 ? 1 : k * c;
+  if (p->bulk == BULK_BF16X3) {
+    KF_TRY((copy2d<double, float>(p->s, p->P64, p->ldN, (const float*)p->slot_ptr(t0), p->ldN, p->N, p->N)));
+    KF_TRY(predict_cov64(p, p->P64));
+    for (int64_t t = t0 + 1; t <= t1; ++t) KF_TRY(filter_step_mixed(p, t, nullptr, nullptr));
+    p->seg_id = k;
+    return KF_OK;
+  }
   KF_TRY(predict_cov<B>(p, (const B*)p->slot_ptr(t0), (B*)p->P));
   for (int64_t t = t0 + 1; t <= t1; ++t) KF_TRY(filter_step<B>(p, t, nullptr, nullptr));
   p->seg_id = k;
@@ -480,6 +598,8 @@ kf_status run_filter(kf_plan_s* p, const double* Y, const double* x0, const doub
     double* dg = diagP_filt ? diagP_filt + (t - 1) * N : nullptr;
     if (t == 1 && sizeof(B) == 4)
       KF_TRY(filter_first_fp64(p, P0, Y, dg));
+    else if (p->bulk == BULK_BF16X3)
+      KF_TRY(filter_step_mixed(p, t, Y + (t - 1) * m, dg));
     else
       KF_TRY(filter_step<B>(p, t, Y + (t - 1) * m, dg));
     if (p->ckpt > 1 && t % p->ckpt != 0) p->seg_id = t / p->ckpt;

@@ -284,34 +284,57 @@ kf_status split_bf16_t(cudaStream_t s, int64_t rows, int64_t cols, const float* 
 }
 
 // One 32 x 32 output tile of the planes per CTA; blockIdx.z picks the operand.
-__global__ void split_bf16_pair_kernel(SplitOp a, SplitOp b, int n, int64_t ldh) {
-  __shared__ float tile[32][33];
-  const SplitOp& op = blockIdx.z == 0 ? a : b;
+// The first slice of a float64 source is taken in float64 (so the next slices
+// keep bits below float32's), the rest in float32 arithmetic, which is exact
+// for these residuals.
+template <typename S>
+__device__ __forceinline__ void split_tile(const SplitOp& op, int n, int64_t ldh, S (*tile)[33]) {
   const int64_t r0 = (int64_t)blockIdx.x * 32, k0 = (int64_t)blockIdx.y * 32;
-  if (r0 >= op.rows || k0 >= ldh) return;
   const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;  // 32 x 8 threads
+  const S* src = static_cast<const S*>(op.src);
   if (op.trans) {
     for (int i = ty; i < 32; i += 8) {
       const int64_t k = k0 + i, r = r0 + tx;
-      tile[i][tx] = (k < op.cols && r < op.rows) ? op.src[k * op.ld + r] : 0.0f;
+      tile[i][tx] = (k < op.cols && r < op.rows) ? src[k * op.ld + r] : S(0);
     }
   } else {
     for (int i = ty; i < 32; i += 8) {
       const int64_t r = r0 + i, k = k0 + tx;
-      tile[tx][i] = (k < op.cols && r < op.rows) ? op.src[r * op.ld + k] : 0.0f;
+      tile[tx][i] = (k < op.cols && r < op.rows) ? src[r * op.ld + k] : S(0);
     }
   }
   __syncthreads();
   for (int i = ty; i < 32; i += 8) {
     const int64_t r = r0 + i, k = k0 + tx;
     if (r >= op.rows || k >= ldh) continue;
-    float v = tile[tx][i];
-    for (int s = 0; s < n; ++s) {
-      __nv_bfloat16 h = __float2bfloat16_rn(v);
+    const S v0 = tile[tx][i];
+    float v;
+    if (sizeof(S) == 8) {
+      const __nv_bfloat16 h = __double2bfloat16((double)v0);
+      op.planes[0][r * ldh + k] = h;
+      v = (float)((double)v0 - (double)__bfloat162float(h));
+    } else {
+      const __nv_bfloat16 h = __float2bfloat16_rn((float)v0);
+      op.planes[0][r * ldh + k] = h;
+      v = (float)v0 - __bfloat162float(h);
+    }
+    for (int s = 1; s < n; ++s) {
+      const __nv_bfloat16 h = __float2bfloat16_rn(v);
       op.planes[s][r * ldh + k] = h;
       v -= __bfloat162float(h);
     }
   }
+}
+
+__global__ void split_bf16_pair_kernel(SplitOp a, SplitOp b, int n, int64_t ldh) {
+  __shared__ double tile_d[32][33];
+  const SplitOp& op = blockIdx.z == 0 ? a : b;
+  const int64_t r0 = (int64_t)blockIdx.x * 32, k0 = (int64_t)blockIdx.y * 32;
+  if (r0 >= op.rows || k0 >= ldh) return;
+  if (op.f64)
+    split_tile<double>(op, n, ldh, tile_d);
+  else
+    split_tile<float>(op, n, ldh, reinterpret_cast<float(*)[33]>(tile_d));
 }
 
 kf_status split_bf16_pair(cudaStream_t s, const SplitOp& a, const SplitOp& b, int n, int64_t ldh) {

@@ -38,7 +38,7 @@ namespace {
 constexpr int BM = 128;
 constexpr int BK = 64;          // one 128-byte swizzle atom of bf16
 constexpr int UMMA_K = 16;
-constexpr int NUM_THREADS = 192;
+constexpr int NUM_THREADS = 320;  // TMA warp, MMA warp, 8 epilogue warps
 constexpr uint64_t WAIT_NS = 2000000000ull;
 
 template <int BN, int S>  // S = bf16 slices per operand: 2 -> 3 products, 3 -> 6 products
@@ -48,7 +48,7 @@ struct TcCfg {
   static constexpr int STAGE_BYTES = S * A_BYTES + S * B_BYTES;
   static constexpr int STAGES = (200 * 1024) / STAGE_BYTES;
   static_assert(STAGES >= 2, "need a double-buffered pipeline");
-  static constexpr int TMEM_COLS = BN;          // float32 accumulator, one column per output column
+  static constexpr int TMEM_COLS = 2 * BN;      // two float32 accumulators (ping-pong between chunks)
   static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
   // instruction descriptor: D = f32, A = B = bf16, both K-major, N >> 3, M >> 4
   static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
@@ -153,10 +153,16 @@ struct TcMaps {
   CUtensorMap a[3], b[3];  // bf16 planes of A and B, most significant first
 };
 
-template <int BN, int S>
+constexpr int KC = 2;  // k-tiles accumulated in TMEM before promotion to registers
+
+// Epilogue threads: warps 2..9.  Warp w reads TMEM lanes 32*(w%4)..+31 (its
+// lane quadrant) and one half of the BN columns, so each output row is owned
+// by one thread per column half.
+template <int BN, int S, typename TE>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
-    tc_gemm_kernel(const __grid_constant__ TcMaps maps, const GemmParams<float> p, int num_k_tiles) {
+    tc_gemm_kernel(const __grid_constant__ TcMaps maps, const GemmParams<TE> p, int num_k_tiles) {
   using C = TcCfg<BN, S>;
+  constexpr int HALF = BN / 2;
   extern __shared__ uint8_t smem_raw[];
   const int tn = blockIdx.x, tm = blockIdx.y;
   const int m0 = tm * BM, n0 = tn * BN;
@@ -167,8 +173,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   const uint32_t bars = base + C::STAGES * C::STAGE_BYTES;
   auto full_bar = [&](int s) { return bars + 8u * s; };
   auto empty_bar = [&](int s) { return bars + 8u * (C::STAGES + s); };
-  const uint32_t accum_bar = bars + 8u * (2 * C::STAGES);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + C::STAGES * C::STAGE_BYTES + 8 * (2 * C::STAGES + 1));
+  auto accf_bar = [&](int b) { return bars + 8u * (2 * C::STAGES + b); };      // accumulator b ready
+  auto acce_bar = [&](int b) { return bars + 8u * (2 * C::STAGES + 2 + b); };  // accumulator b drained
+  const uint32_t done_bar = bars + 8u * (2 * C::STAGES + 4);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + C::STAGES * C::STAGE_BYTES + 8 * (2 * C::STAGES + 5));
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   volatile int* skip_flag = reinterpret_cast<volatile int*>(tmem_slot + 2);
   volatile int never = 0;  // abort flag for the clean-up waits, which must not stop early
@@ -179,7 +187,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       mbar_init(full_bar(s), 1);
       mbar_init(empty_bar(s), 1);
     }
-    mbar_init(accum_bar, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(accf_bar(b), 1);
+      mbar_init(acce_bar(b), 8);
+    }
+    mbar_init(done_bar, 1);
     *abort_flag = 0;
     *skip_flag = status_failed(p.status) ? 1 : 0;  // read once, shared by the whole CTA
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -202,6 +214,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   if (p.tri_b > 0) kt1 = min(kt1, (n0 + BN + BK - 1) / BK);
   if (p.tri_b < 0) kt0 = max(kt0, n0 / BK);
   const int nk = kt1 > kt0 ? kt1 - kt0 : 0;
+  const int nchunks = (nk + KC - 1) / KC;
+  bool mma_issued = false;
 
   if (skip) {
     // an earlier kernel failed: do nothing but release TMEM below
@@ -231,19 +245,25 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         if (last_round[s] >= 0) mbar_wait(full_bar(s), (uint32_t)last_round[s] & 1u, &never);
     }
   } else if (warp == 1 && lane == 0) {
-    // ---------------- MMA issuer
-    bool ok = true;
+    // ---------------- MMA issuer: chunk c accumulates into TMEM buffer c & 1
     for (int it = 0; it < nk; ++it) {
+      const int c = it / KC, buf = c & 1;
+      if (it % KC == 0 && !mbar_wait(acce_bar(buf), ((uint32_t)(c >> 1) & 1u) ^ 1u, abort_flag)) {
+        *abort_flag = 1;
+        status_set(p.status, KF_ERR_TIMEOUT, p.step, 4);
+        break;
+      }
       const int s = it % C::STAGES;
       const uint32_t ph = (uint32_t)(it / C::STAGES) & 1u;
       if (!mbar_wait(full_bar(s), ph, abort_flag)) {
         *abort_flag = 1;
         status_set(p.status, KF_ERR_TIMEOUT, p.step, 2);
-        ok = false;
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t st = base + s * C::STAGE_BYTES;
+      const uint32_t dacc = tmem + (uint32_t)(buf * BN);
+      const bool first_of_chunk = (it % KC) == 0;
 #pragma unroll
       for (int k = 0; k < BK / UMMA_K; ++k) {
         const uint32_t off = k * UMMA_K * 2;  // bytes along K inside the swizzle atom
@@ -253,50 +273,61 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 #pragma unroll
           for (int i = 0; i <= lvl; ++i) {
             const int j = lvl - i;
-            const uint32_t acc = (it > 0 || k > 0 || lvl != S - 1 || i != 0) ? 1u : 0u;
-            mma_bf16(tmem, smem_desc(st + i * C::A_BYTES + off), smem_desc(st + S * C::A_BYTES + j * C::B_BYTES + off),
+            const uint32_t acc = (!first_of_chunk || k > 0 || lvl != S - 1 || i != 0) ? 1u : 0u;
+            mma_bf16(dacc, smem_desc(st + i * C::A_BYTES + off), smem_desc(st + S * C::A_BYTES + j * C::B_BYTES + off),
                      C::IDESC, acc);
           }
         }
       }
+      mma_issued = true;
       mma_commit(empty_bar(s));
+      if (it % KC == KC - 1 || it == nk - 1) mma_commit(accf_bar(buf));
     }
-    mma_commit(accum_bar);
-    (void)ok;
   } else if (warp >= 2) {
-    // ---------------- epilogue: warp w reads TMEM lanes 32*(w%4) .. +31
-    const int lane_base = 32 * (warp % 4);
-    bool ready = nk > 0 ? mbar_wait(accum_bar, 0, abort_flag) : true;
-    if (!ready && !*abort_flag) {
-      *abort_flag = 1;
-      status_set(p.status, KF_ERR_TIMEOUT, p.step, 3);
-    }
-    if (ready) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int gi = m0 + lane_base + lane;
-#pragma unroll 1
-      for (int c = 0; c < BN; c += 32) {
-        uint32_t r[32];
-        if (nk > 0) {
-          tmem_ld32(tmem + ((uint32_t)lane_base << 16) + (uint32_t)c, r);
-        } else {
+    // ---------------- epilogue: promote each chunk into float32 registers, then store
+    const int q = warp % 4, h = (warp - 2) / 4;
+    const int gi = m0 + 32 * q + lane;
+    float acc[HALF];
 #pragma unroll
-          for (int j = 0; j < 32; ++j) r[j] = 0u;
+    for (int j = 0; j < HALF; ++j) acc[j] = 0.0f;
+    bool ok = true;
+    for (int c = 0; c < nchunks && ok; ++c) {
+      const int buf = c & 1;
+      if (!mbar_wait(accf_bar(buf), (uint32_t)(c >> 1) & 1u, abort_flag)) {
+        if (!*abort_flag) {
+          *abort_flag = 1;
+          status_set(p.status, KF_ERR_TIMEOUT, p.step, 3);
         }
-        if (gi < p.M) {
-#pragma unroll 4
-          for (int j = 0; j < 32; ++j) {
-            const int gj = n0 + c + j;
-            if (gj >= p.N) break;
-            if (p.sym && gj > gi) break;
-            epilogue_store(p, gi, gj, __uint_as_float(r[j]));
-          }
-        }
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+      for (int j = 0; j < HALF; j += 32) {
+        uint32_t r[32];
+        tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * BN + h * HALF + j), r);
+#pragma unroll
+        for (int e = 0; e < 32; ++e) acc[j + e] += __uint_as_float(r[e]);
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(acce_bar(buf)) : "memory");
+    }
+    if (ok && gi < p.M) {
+#pragma unroll
+      for (int j = 0; j < HALF; ++j) {
+        const int gj = n0 + h * HALF + j;
+        if (gj < p.N && !(p.sym && gj > gi)) epilogue_store(p, gi, gj, (TE)acc[j]);
       }
     }
   }
-  // after an abort, make sure every issued MMA has finished before TMEM is freed
-  if (!skip && warp == 1 && lane == 0 && *abort_flag) mbar_wait(accum_bar, 0, &never);
+  // every issued MMA must have finished before TMEM is freed
+  if (!skip && warp == 1 && lane == 0) {
+    if (mma_issued) {
+      mma_commit(done_bar);
+      mbar_wait(done_bar, 0, &never);
+    }
+  }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 1) {
@@ -343,8 +374,8 @@ kf_status make_map(CUtensorMap* map, const void* ptr, int64_t rows, int64_t cols
   return r == CUDA_SUCCESS ? KF_OK : KF_ERR_CUDA;
 }
 
-template <int BN, int S>
-kf_status launch(cudaStream_t s, const GemmParams<float>& g, const TcScratch& sc, int64_t ldk) {
+template <int BN, int S, typename TE>
+kf_status launch(cudaStream_t s, const GemmParams<TE>& g, const TcScratch& sc, int64_t ldk) {
   using C = TcCfg<BN, S>;
   TcMaps maps;
   for (int i = 0; i < S; ++i) {
@@ -353,14 +384,40 @@ kf_status launch(cudaStream_t s, const GemmParams<float>& g, const TcScratch& sc
   }
   static bool configured = false;
   if (!configured) {
-    KF_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<BN, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
+    KF_CUDA_TRY(
+        cudaFuncSetAttribute(tc_gemm_kernel<BN, S, TE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
     configured = true;
   }
   dim3 grid((unsigned)ceil_div(g.N, BN), (unsigned)ceil_div(g.M, BM));
   const int num_k_tiles = (int)(ldk / BK);
-  tc_gemm_kernel<BN, S><<<grid, NUM_THREADS, C::SMEM, s>>>(maps, g, num_k_tiles);
+  tc_gemm_kernel<BN, S, TE><<<grid, NUM_THREADS, C::SMEM, s>>>(maps, g, num_k_tiles);
   ++g_launches;
   return launch_check("tc_gemm");
+}
+
+template <typename TE>
+kf_status run_split(cudaStream_t s, TcScratch& sc, const TcOperand& A, const TcOperand& B, const GemmParams<TE>& g,
+                    int slices) {
+  if (g.M <= 0 || g.N <= 0) return KF_OK;
+  if (g.sym && g.M != g.N) return KF_ERR_ARG;
+  if (slices != 2 && slices != 3) return KF_ERR_ARG;
+  if (g.K == 0) {  // epilogue only: no operand tiles to load
+    GemmParams<TE> h = g;
+    h.transA = 0;
+    return gemm_simt<TE>(s, true, h);
+  }
+  const int64_t ldk = round_up(g.K, BK);
+  if (g.M > sc.rows || g.N > sc.rows || ldk > sc.ld) return KF_ERR_ARG;
+  SplitOp oa, ob;
+  oa.src = A.p; oa.ld = A.ld; oa.rows = g.M; oa.cols = g.K; oa.trans = A.trans; oa.f64 = A.f64;
+  ob.src = B.p; ob.ld = B.ld; ob.rows = g.N; ob.cols = g.K; ob.trans = B.trans; ob.f64 = B.f64;
+  for (int i = 0; i < slices; ++i) {
+    oa.planes[i] = sc.a[i];
+    ob.planes[i] = sc.b[i];
+  }
+  KF_TRY(split_bf16_pair(s, oa, ob, slices, ldk));
+  if (slices == 2) return launch<256, 2, TE>(s, g, sc, ldk);
+  return launch<128, 3, TE>(s, g, sc, ldk);
 }
 
 }  // namespace
@@ -394,26 +451,18 @@ bool tc_available() {
 }
 
 kf_status tc_gemm_split(cudaStream_t s, TcScratch& sc, const GemmParams<float>& g, int slices, bool transB) {
-  if (g.M <= 0 || g.N <= 0) return KF_OK;
-  if (g.sym && g.M != g.N) return KF_ERR_ARG;
-  if (slices != 2 && slices != 3) return KF_ERR_ARG;
-  if (g.K == 0) {  // epilogue only: no operand tiles to load
-    GemmParams<float> h = g;
-    h.transA = 0;
-    return gemm_simt<float>(s, true, h);
-  }
-  const int64_t ldk = round_up(g.K, BK);
-  if (g.M > sc.rows || g.N > sc.rows || ldk > sc.ld) return KF_ERR_ARG;
-  SplitOp oa, ob;
-  oa.src = g.A; oa.ld = g.lda; oa.rows = g.M; oa.cols = g.K; oa.trans = g.transA;
-  ob.src = g.B; ob.ld = g.ldb; ob.rows = g.N; ob.cols = g.K; ob.trans = transB ? 0 : 1;
-  for (int i = 0; i < slices; ++i) {
-    oa.planes[i] = sc.a[i];
-    ob.planes[i] = sc.b[i];
-  }
-  KF_TRY(split_bf16_pair(s, oa, ob, slices, ldk));
-  if (slices == 2) return launch<256, 2>(s, g, sc, ldk);
-  return launch<128, 3>(s, g, sc, ldk);
+  TcOperand A{g.A, g.lda, 0, g.transA}, B{g.B, g.ldb, 0, transB ? 0 : 1};
+  return run_split<float>(s, sc, A, B, g, slices);
+}
+
+kf_status tc_gemm_ops(cudaStream_t s, TcScratch& sc, const TcOperand& A, const TcOperand& B,
+                      const GemmParams<double>& epi, int slices) {
+  return run_split<double>(s, sc, A, B, epi, slices);
+}
+
+kf_status tc_gemm_ops(cudaStream_t s, TcScratch& sc, const TcOperand& A, const TcOperand& B,
+                      const GemmParams<float>& epi, int slices) {
+  return run_split<float>(s, sc, A, B, epi, slices);
 }
 
 }  // namespace kfm

@@ -26,8 +26,28 @@ bool tc_available();
 // split into `slices` bf16 planes (2 or 3), transposing on the way where
 // needed, and the products of slice levels i + j < slices are accumulated in
 // float32 on the tensor cores (3 products for 2 slices, 6 for 3), followed by
-// the epilogue of GemmParams.  g.tri_a / g.tri_b skip zero k-tiles of
+// the epilogue of GemmParams.  The tensor-core accumulator is promoted into
+// float32 registers every two 64-wide k-tiles: the tensor cores' own
+// accumulation truncates, a bias that would otherwise grow with K.  g.tri_a / g.tri_b skip zero k-tiles of
 // triangular operands.
 kf_status tc_gemm_split(cudaStream_t s, TcScratch& sc, const GemmParams<float>& g, int slices, bool transB = true);
+
+// An operand given by pointer, leading dimension, precision and orientation:
+// the product uses rows of op = (trans ? X^T : X), each of K elements.
+struct TcOperand {
+  const void* p;
+  int64_t ld;
+  int f64;    // 1: float64 data (split from its float64 value), 0: float32
+  int trans;  // 1: X is stored K x rows and used transposed
+};
+
+// As tc_gemm_split with separately described operands; the epilogue (and
+// its cin / out / out2) is float64 or float32.  The A / B / transA fields of
+// epi are ignored.  Float64 epilogues add the float32 products to float64
+// values, which keeps the covariance itself at float64 precision.
+kf_status tc_gemm_ops(cudaStream_t s, TcScratch& sc, const TcOperand& A, const TcOperand& B,
+                      const GemmParams<double>& epi, int slices);
+kf_status tc_gemm_ops(cudaStream_t s, TcScratch& sc, const TcOperand& A, const TcOperand& B,
+                      const GemmParams<float>& epi, int slices);
 
 }  // namespace kfm
