@@ -153,7 +153,7 @@ struct TcMaps {
   CUtensorMap a[3], b[3];  // bf16 planes of A and B, most significant first
 };
 
-constexpr int KC = 2;  // k-tiles accumulated in TMEM before promotion to registers
+constexpr int KC = 1;  // k-tiles accumulated in TMEM before promotion to registers
 
 // Epilogue threads: warps 2..9.  Warp w reads TMEM lanes 32*(w%4)..+31 (its
 // lane quadrant) and one half of the BN columns, so each output row is owned

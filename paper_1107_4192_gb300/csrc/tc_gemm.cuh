@@ -27,7 +27,7 @@ bool tc_available();
 // needed, and the products of slice levels i + j < slices are accumulated in
 // float32 on the tensor cores (3 products for 2 slices, 6 for 3), followed by
 // the epilogue of GemmParams.  The tensor-core accumulator is promoted into
-// float32 registers every two 64-wide k-tiles: the tensor cores' own
+// float32 registers after every 64-wide k-tile: the tensor cores' own
 // accumulation truncates, a bias that would otherwise grow with K.  g.tri_a / g.tri_b skip zero k-tiles of
 // triangular operands.
 kf_status tc_gemm_split(cudaStream_t s, TcScratch& sc, const GemmParams<float>& g, int slices, bool transB = true);
