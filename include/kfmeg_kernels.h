@@ -35,6 +35,22 @@ kf_status kfx_gemm(int32_t dtype, int32_t transB, int32_t sym, int64_t M, int64_
 kf_status kfx_posv_right(int32_t dtype, int64_t n, void* A, int64_t lda, int64_t M, void* B,
                          int64_t ldb, int64_t* fail_index, void* stream);
 
+/* kfx_posv_right without device allocation, for callers that cannot call
+ * cudaMalloc / cudaFree when the solve runs (device memory reserved up front
+ * by another allocator; loops where cudaFree's device-wide synchronisation
+ * would stall other streams).  The paper has no counterpart: this is a
+ * calling convention of the library, not part of the method.  Scratch lives
+ * in one static device array of about 2 MiB that every GPU loading the
+ * library keeps until exit, so n <= KFX_POSV_STATIC_MAX_N (larger n returns
+ * KF_ERR_ARG before any GPU work).  All calls share that array: calls whose
+ * GPU work overlaps (other threads or unordered streams) race and must be
+ * ordered by the caller.  The first call on each device looks up the array's
+ * address and should come before any stream capture.  Arguments and results
+ * as kfx_posv_right. */
+#define KFX_POSV_STATIC_MAX_N 4096
+kf_status kfx_posv_right_static(int32_t dtype, int64_t n, void* A, int64_t lda, int64_t M, void* B,
+                                int64_t ldb, int64_t* fail_index, void* stream);
+
 /* out = F P F^T + Q for F in compressed-row form (rowptr: N+1, col/val: nnz),
  * the mesh-coupled prediction of eqns 2-3 / eqn 7.  dtype 0 or 1 for P / out;
  * Q per q_kind (kf_cov_kind, float64, NULL allowed with q_kind = -1). */

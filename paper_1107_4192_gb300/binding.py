@@ -64,6 +64,7 @@ _SIGS = {
     "kf_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "kfx_gemm": (ctypes.c_int, [_I32, _I32, _I32, _I64, _I64, _I64, _D, _P, _I64, _P, _I64, _D, _P, _I64, _P]),
     "kfx_posv_right": (ctypes.c_int, [_I32, _I64, _P, _I64, _I64, _P, _I64, ctypes.POINTER(_I64), _P]),
+    "kfx_posv_right_static": (ctypes.c_int, [_I32, _I64, _P, _I64, _I64, _P, _I64, ctypes.POINTER(_I64), _P]),
     "kfx_spmm_fpft": (ctypes.c_int, [_I32, _I64, _P, _P, _P, _P, _I64, _P, _I64, _I32, _P, _P]),
     "kfx_split_bf16": (ctypes.c_int, [_I64, _I64, _P, _I64, _P, _P, _I64, _P]),
 }
@@ -219,6 +220,13 @@ def kfx_gemm(dtype, transB, sym, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s
 def kfx_posv_right(dtype, n, A, lda, M, B, ldb, stream=None):
     fi = _I64()
     st = lib().kfx_posv_right(dtype, n, _ptr(A), lda, M, _ptr(B), ldb, ctypes.byref(fi), _stream(stream))
+    return st, fi.value
+
+
+def kfx_posv_right_static(dtype, n, A, lda, M, B, ldb, stream=None):
+    """kfx_posv_right with scratch in a static device array (no allocation); n <= 4096."""
+    fi = _I64()
+    st = lib().kfx_posv_right_static(dtype, n, _ptr(A), lda, M, _ptr(B), ldb, ctypes.byref(fi), _stream(stream))
     return st, fi.value
 
 
