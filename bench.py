@@ -238,7 +238,7 @@ def main():
         dist.barrier()
     elapsed = ev0.elapsed_time(ev1) / 1e3
     launches = B.kf_plan_launch_count(plan.handle) - launches0
-    prof = {c: B.kf_plan_profile_read(plan.handle, c) for c in range(7)}
+    prof = {c: B.kf_plan_profile_read(plan.handle, c) for c in range(8)}
     B.kf_plan_profile(plan.handle, False)
     if world > 1:
         t = torch.tensor([elapsed], device="cuda", dtype=torch.float64)
@@ -272,32 +272,30 @@ def main():
     ms_per_step = elapsed / args.steps * 1e3
     peaks, peak_src = load_peaks()
 
-    # dominant kernel class by device time inside the timed region
-    names = {0: "filter_update", 1: "innovation", 2: "smoother_gemm", 3: "smoother_solve", 4: "predict",
-             5: "solve_factor", 6: "solve_gain"}
-    dom = max((c for c in prof if c < 5), key=lambda c: prof[c][1])
-    n_l, ms_l = prof[dom]
-    avg_s = ms_l / 1e3 / max(n_l, 1)
-    if dom == 2:
-        work = smoother_gemm_flops_per_launch(N)
-        if args.prec == "mixed":
-            roof = {"bound": "tensor", "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s"}
-        else:
-            roof = {"bound": "alu", "peak": 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12 /
-                    (1 if args.prec == "fp32" else 64), "unit": "TFLOP/s"}
-        achieved = work / avg_s / 1e12
-    elif dom == 3:
-        work = (N ** 3 / 3 + 2 * N ** 3)
-        per_elt_peak = 1.25 if args.solve == "fp64" or args.prec == "fp64" else \
-            152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        roof = {"bound": "alu", "peak": per_elt_peak, "unit": "TFLOP/s"}
-        achieved = work / avg_s / 1e12
+    # Roofline of the smoother's N x N covariance products (W = J D and P + W J^T): in the mixed
+    # mode these are the tcgen05 split-bf16 kernel launches timed alone (class 7); otherwise the
+    # phase of the same two products on the CUDA cores.
+    if args.prec == "mixed" and prof[7][0] > 0:
+        n_l, ms_l = prof[7]
+        kname = "tc_gemm_kernel<256,2> (split-bf16 W = J D, P + W J^T)"
+        # bf16x3 spends three bf16 products per product: its peak is a third of the measured
+        # sustained bf16 dense peak
+        roof = {"bound": "tensor", "peak": peaks["bf16_tflops_sustained"] / 3, "unit": "TFLOP/s",
+                "peak_note": "bf16_tflops_sustained / 3 (three bf16 products per split-bf16 product)"}
     else:
-        byt = {0: 3.0, 1: 1.0, 4: 2.0}[dom] * N * N * (8 if args.prec == "fp64" else 4)
-        roof = {"bound": "hbm", "peak": peaks["hbm_gbs"], "unit": "GB/s"}
-        achieved = byt / avg_s / 1e9
-    roof.update({"kernel": names[dom], "achieved": achieved, "frac": achieved / roof["peak"], "traffic": None,
-                 "peak_source": peak_src, "launches": n_l, "avg_launch_ms": avg_s * 1e3})
+        n_l, ms_l = prof[2]
+        kname = "gemm_simt (W = J D, P + W J^T)"
+        alu = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        roof = {"bound": "alu", "peak": alu if args.prec == "fp32" else 1.25, "unit": "TFLOP/s",
+                "peak_note": "152 SMs x 128 FP32 lanes x 2 x max SM clock" if args.prec == "fp32" else
+                "FP64 nominal 1.25 TFLOP/s"}
+    avg_s = ms_l / 1e3 / max(n_l, 1)
+    achieved = smoother_gemm_flops_per_launch(N) / avg_s / 1e12
+    roof.update({"kernel": kname, "achieved": achieved, "frac": achieved / roof["peak"], "traffic": None,
+                 "peak_source": peak_src, "launches": n_l, "avg_launch_ms": avg_s * 1e3,
+                 "work_per_launch": "(2 N^3 + N^2 (N+1)) / 2 flops, N = 8196"})
+    names = {0: "filter_update", 1: "innovation", 2: "smoother_gemm", 3: "smoother_solve", 4: "predict",
+             5: "solve_factor", 6: "solve_gain", 7: "smoother_gemm_kernel"}
 
     line = {"metric": METRIC, "value": value, "unit": "timesteps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",

@@ -176,7 +176,9 @@ typedef enum {
   KF_KC_SOLVE_FACTOR = 5,    /* inside SMOOTH_SOLVE: Cholesky (+ inverse) of       */
                              /* P_{t+1|t}                                          */
   KF_KC_SOLVE_GAIN = 6,      /* inside SMOOTH_SOLVE: forming J_t from the factor   */
-  KF_KC_COUNT = 7
+  KF_KC_SMOOTH_GEMM_KERNEL = 7, /* inside SMOOTH_GEMM, mixed mode: the tensor-core */
+                             /* kernel launches alone (one mark per launch)        */
+  KF_KC_COUNT = 8
 } kf_kernel_class;
 kf_status kf_plan_profile(kf_plan_t p, int32_t enable);
 kf_status kf_plan_profile_read(kf_plan_t p, int32_t cls, int64_t* launches,

@@ -24,7 +24,7 @@ KF_PREC_FP64, KF_PREC_FP32, KF_PREC_MIXED_BF16X3 = 0, 1, 2
 KF_SOLVE_FP64, KF_SOLVE_FP32 = 0, 1
 KF_COV_SCALAR, KF_COV_DIAG, KF_COV_DENSE = 0, 1, 2
 KF_KC_FILTER_UPDATE, KF_KC_INNOVATION, KF_KC_SMOOTH_GEMM, KF_KC_SMOOTH_SOLVE, KF_KC_PREDICT, \
-    KF_KC_SOLVE_FACTOR, KF_KC_SOLVE_GAIN = range(7)
+    KF_KC_SOLVE_FACTOR, KF_KC_SOLVE_GAIN, KF_KC_SMOOTH_GEMM_KERNEL = range(8)
 
 
 class KfDesc(ctypes.Structure):

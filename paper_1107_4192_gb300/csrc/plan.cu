@@ -226,6 +226,38 @@ struct Prof {
   }
 };
 
+// Times the tensor-core kernel launches alone while installed (class cls).
+struct KernelTimer : TcLaunchTimer {
+  kf_plan_s* p;
+  int cls;
+  cudaEvent_t a = nullptr;
+  KernelTimer(kf_plan_s* plan, int c) : p(plan), cls(c) {
+    if (p->prof) g_tc_timer = this;
+  }
+  ~KernelTimer() override {
+    if (g_tc_timer == this) g_tc_timer = nullptr;
+  }
+  cudaEvent_t take() {
+    if (!p->pool.empty()) {
+      cudaEvent_t e = p->pool.back();
+      p->pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+  }
+  void before(cudaStream_t s) override {
+    a = take();
+    cudaEventRecord(a, s);
+  }
+  void after(cudaStream_t s) override {
+    cudaEvent_t b = take();
+    cudaEventRecord(b, s);
+    p->marks.push_back({cls, a, b});
+  }
+};
+
 // ------------------------------------------------------------ GEMM dispatch
 
 // Bulk products: float64 / float32 on the CUDA cores, or split-bf16 on the
@@ -732,6 +764,7 @@ kf_status run_smoother(kf_plan_s* p, double* x_smooth, double* diagP_smooth, dou
     if ((void*)Jm != (void*)Jb) KF_TRY((copy2d<B, V>(s, Jm, ldN, Jb, ldN, N, N)));
     {
       Prof pr(p, KF_KC_SMOOTH_GEMM);
+      KernelTimer kt(p, KF_KC_SMOOTH_GEMM_KERNEL);
       GemmParams<B> w;  // W = J_t D_{t+1}  (D symmetric)
       w.M = (int)N; w.N = (int)N; w.K = (int)N;
       w.A = Jm; w.lda = ldN;
@@ -745,6 +778,7 @@ kf_status run_smoother(kf_plan_s* p, double* x_smooth, double* diagP_smooth, dou
     KF_TRY(predict_cov<B>(p, Ptm1, Pn));  // P_{t|t-1}
     {
       Prof pr(p, KF_KC_SMOOTH_GEMM);
+      KernelTimer kt(p, KF_KC_SMOOTH_GEMM_KERNEL);
       GemmParams<B> g;  // D_t = P_{t|t} + W J_t^T - P_{t|t-1};  diag(P_{t|T}) out
       g.M = (int)N; g.N = (int)N; g.K = (int)N;
       g.A = Wb; g.lda = ldN;

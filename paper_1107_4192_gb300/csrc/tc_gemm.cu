@@ -390,7 +390,9 @@ kf_status launch(cudaStream_t s, const GemmParams<TE>& g, const TcScratch& sc, i
   }
   dim3 grid((unsigned)ceil_div(g.N, BN), (unsigned)ceil_div(g.M, BM));
   const int num_k_tiles = (int)(ldk / BK);
+  if (g_tc_timer) g_tc_timer->before(s);
   tc_gemm_kernel<BN, S, TE><<<grid, NUM_THREADS, C::SMEM, s>>>(maps, g, num_k_tiles);
+  if (g_tc_timer) g_tc_timer->after(s);
   ++g_launches;
   return launch_check("tc_gemm");
 }
@@ -421,6 +423,8 @@ kf_status run_split(cudaStream_t s, TcScratch& sc, const TcOperand& A, const TcO
 }
 
 }  // namespace
+
+thread_local TcLaunchTimer* g_tc_timer = nullptr;
 
 uint64_t tc_scratch_bytes(int64_t rows, int64_t ld) { return 6ull * rows * ld * sizeof(__nv_bfloat16); }
 

@@ -18,6 +18,15 @@ uint64_t tc_scratch_bytes(int64_t rows, int64_t ld);
 kf_status tc_scratch_alloc(TcScratch& sc, int64_t rows, int64_t ld,
                            const std::function<kf_status(void**, size_t)>& alloc);
 
+// Optional event timing of the tensor-core kernel launches alone (without the
+// operand split), installed by a plan while it profiles a phase.
+struct TcLaunchTimer {
+  virtual void before(cudaStream_t s) = 0;
+  virtual void after(cudaStream_t s) = 0;
+  virtual ~TcLaunchTimer() = default;
+};
+extern thread_local TcLaunchTimer* g_tc_timer;
+
 // True when this build carries the tcgen05 kernels.
 bool tc_available();
 
