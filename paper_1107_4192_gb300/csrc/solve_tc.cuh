@@ -16,4 +16,10 @@ kf_status chol_inverse_tc(cudaStream_t s, TcScratch& sc, int n, float* L, int64_
 kf_status gain_from_inverse_tc(cudaStream_t s, TcScratch& sc, int n, const float* Bm, int64_t ldb, const float* W,
                                int64_t ldw, float* Z, int64_t ldz, float* J, int64_t ldj, int* status);
 
+// F = I with Q = q I or diagonal: J = P_{t|t} (P_{t|t} + Q)^{-1} = I - Q P_{t+1|t}^{-1},
+// with P_{t+1|t}^{-1} = W^T W formed on the lower triangle (n^3 / 3 instead of
+// the 2 n^3 of the two triangular products).  Pinv is n x n scratch.
+kf_status gain_identity_tc(cudaStream_t s, TcScratch& sc, int n, const float* W, int64_t ldw, int q_kind,
+                           const double* q, float* Pinv, int64_t ldp, float* J, int64_t ldj, int* status);
+
 }  // namespace kfm
