@@ -96,60 +96,68 @@ __global__ void __launch_bounds__(256, 1) potrf_diag_kernel(T* A, int64_t lda, i
     const int j0 = p * 32;
     // (a) one warp: factor and invert the 32 x 32 diagonal block
     if (warp == 0) {
-      // Lane i holds row i of the 32 x 32 block in registers.  Step j scales
-      // column j, publishes it in shared memory (Tb) and every lane applies the
-      // rank-1 update to its row from broadcast loads, which are independent
-      // of each other and so overlap.
-      T a[32];
-#pragma unroll
-      for (int k = 0; k < 32; ++k) a[k] = k <= lane ? S[(j0 + lane) * LD + j0 + k] : T(0);
+      // Right-looking factorisation of the 32 x 32 block in shared memory, lane i
+      // owning row i.  The step loop stays rolled (small code); inside a step
+      // the 32 column entries come in registers (shuffles) and the row update
+      // is 32 independent predicated load-fma-store triples.
+      T* P = S + j0 * LD + j0;
+      T* Xp = X + j0 * LD + j0;
       int bad = -1;
-#pragma unroll
       for (int j = 0; j < 32; ++j) {
-        const T d = __shfl_sync(0xffffffffu, a[j], j);
-        if (bad < 0 && !(d > T(0) && d < T(INFINITY))) bad = j;
-        const T ljj = Num<T>::sqrt_(d);
-        if (lane > j) a[j] = a[j] / ljj;
-        if (lane == j) a[j] = ljj;
-        Tb[lane] = a[j];
-        __syncwarp();
-        const T lij = a[j];
-#pragma unroll
-        for (int k = j + 1; k < 32; ++k) {
-          const T lk = Tb[k];
-          if (lane >= k) a[k] = fma(-lij, lk, a[k]);
+        const T d = P[j * LD + j];
+        if (!(d > T(0) && d < T(INFINITY))) {
+          bad = j;
+          break;
         }
+        T ljj, rinv;
+        if constexpr (sizeof(T) == 4) {  // reciprocal square root plus one Newton step (about 1 ulp)
+          float r = rsqrtf((float)d);
+          r = r * (1.5f - 0.5f * (float)d * r * r);
+          rinv = (T)r;
+          ljj = d * rinv;
+        } else {
+          ljj = Num<T>::sqrt_(d);
+          rinv = T(1) / ljj;
+        }
+        T lij = T(0);
+        if (lane > j) lij = P[lane * LD + j] * rinv;
+        else if (lane == j) lij = ljj;
+        if (lane >= j) P[lane * LD + j] = lij;
+        Tb[lane] = lij;  // column j, broadcast through shared memory
         __syncwarp();
+        T col[32];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) col[k] = Tb[k];
+        // branch-free: every lane touches all 32 entries of its row, with the
+        // update masked to j < k <= lane (entries above the diagonal stay zero)
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+          const T w = (k > j && k <= lane) ? lij : T(0);
+          P[lane * LD + k] = fma(-w, col[k], P[lane * LD + k]);
+        }
+        __syncwarp();  // the next pivot is read from another lane's row
       }
+      __syncwarp();
       if (bad >= 0) {
         if (lane == 0) {
           fail = 1;
           status_set(status, KF_ERR_NOT_PD, step, base + j0 + bad);
         }
       } else {
-#pragma unroll
-        for (int k = 0; k < 32; ++k)
-          if (k <= lane) S[(j0 + lane) * LD + j0 + k] = a[k];
-        __syncwarp();
-        // lane c computes column c of the block inverse, x_i = (delta_ic - sum_{k<i} L_ik x_k) / L_ii,
-        // with L_ik broadcast from shared memory
-        const T* P = S + j0 * LD + j0;
-        T x[32];
-#pragma unroll
+        // lane c computes column c of the block inverse, rows in order:
+        // x_i = (delta_ic - sum_{c<=k<i} L_ik x_k) / L_ii
         for (int i = 0; i < 32; ++i) {
-          T acc0 = (i == lane) ? T(1) : T(0), acc1 = T(0), acc2 = T(0), acc3 = T(0);
+          // branch-free: X is zero above its diagonal (k < lane), and k >= i is masked
+          T acc0 = (i == lane) ? T(1) : T(0), acc1 = T(0);
 #pragma unroll
-          for (int k = 0; k < i; ++k) {
-            const T lik = P[i * LD + k];
-            if ((k & 3) == 0) acc0 = fma(-lik, x[k], acc0);
-            else if ((k & 3) == 1) acc1 = fma(-lik, x[k], acc1);
-            else if ((k & 3) == 2) acc2 = fma(-lik, x[k], acc2);
-            else acc3 = fma(-lik, x[k], acc3);
+          for (int k = 0; k < 32; k += 2) {
+            const T l0 = k < i ? P[i * LD + k] : T(0);
+            const T l1 = k + 1 < i ? P[i * LD + k + 1] : T(0);
+            acc0 = fma(-l0, Xp[k * LD + lane], acc0);
+            acc1 = fma(-l1, Xp[(k + 1) * LD + lane], acc1);
           }
-          x[i] = ((acc0 + acc1) + (acc2 + acc3)) / P[i * LD + i];
+          Xp[i * LD + lane] = i >= lane ? (acc0 + acc1) / P[i * LD + i] : T(0);
         }
-#pragma unroll
-        for (int i = 0; i < 32; ++i) X[(j0 + i) * LD + j0 + lane] = x[i];
       }
     }
     __syncthreads();
@@ -160,7 +168,7 @@ __global__ void __launch_bounds__(256, 1) potrf_diag_kernel(T* A, int64_t lda, i
     for (int item = tid; item < R * 8; item += nt) {
       const int i = r0 + item / 8, c0 = (item % 8) * 4;
       T o[4] = {T(0), T(0), T(0), T(0)};
-#pragma unroll 4
+#pragma unroll 8
       for (int k = 0; k < 32; ++k) {
         const T av = S[i * LD + j0 + k];
 #pragma unroll
@@ -188,7 +196,7 @@ __global__ void __launch_bounds__(256, 1) potrf_diag_kernel(T* A, int64_t lda, i
       const int q = item / 256, rr = (item % 256) / 8, c0 = (item % 8) * 4;
       T o[4] = {T(0), T(0), T(0), T(0)};
       for (int kb = 32 * q; kb < 32 * p; kb += 32) {
-#pragma unroll 4
+#pragma unroll 8
         for (int kk = 0; kk < 32; ++kk) {
           const int k = kb + kk;
           const T lv = S[(32 * p + rr) * LD + k];
@@ -203,7 +211,7 @@ __global__ void __launch_bounds__(256, 1) potrf_diag_kernel(T* A, int64_t lda, i
     for (int item = tid; item < p * 32 * 8; item += nt) {
       const int q = item / 256, rr = (item % 256) / 8, c0 = (item % 8) * 4;
       T o[4] = {T(0), T(0), T(0), T(0)};
-#pragma unroll 4
+#pragma unroll 8
       for (int k = 0; k < 32; ++k) {  // X_pp is zero above its diagonal
         const T xv = X[(32 * p + rr) * LD + 32 * p + k];
 #pragma unroll
