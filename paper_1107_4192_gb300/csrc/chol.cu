@@ -8,6 +8,8 @@
 // that inverse, and the trailing lower triangle is updated by a rank-nb
 // product.  The solves reuse the diagonal-block inverses, so every step with
 // O(n^3) work is a tiled product.
+#include <mutex>
+
 #include "ops.cuh"
 
 namespace kfm {
@@ -235,14 +237,14 @@ template <typename T, int NB>
 static kf_status launch_potrf_diag(cudaStream_t s, T* A, int64_t lda, int n, T* dinv, int64_t ldd, int* status,
                                    int step, int base) {
   const size_t smem = DiagSmem<T, NB>::bytes;
-  static bool configured = false;
-  if (!configured) {
-    KF_CUDA_TRY(cudaFuncSetAttribute(potrf_diag_kernel<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem));
-    configured = true;
-  }
+  static std::once_flag configured;
+  static cudaError_t cfg_err = cudaSuccess;
+  std::call_once(configured, [&] {
+    cfg_err = cudaFuncSetAttribute(potrf_diag_kernel<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  });
+  KF_CUDA_TRY(cfg_err);
   potrf_diag_kernel<T, NB><<<1, 256, smem, s>>>(A, lda, n, dinv, ldd, status, step, base);
-  ++g_launches;
+  note_launch();
   return launch_check("potrf_diag");
 }
 

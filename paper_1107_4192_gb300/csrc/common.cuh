@@ -7,6 +7,7 @@
 #include <stdio.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include "../../include/kfmeg.h"
 
@@ -68,7 +69,14 @@ inline kf_status launch_check(const char* what) {
   return KF_OK;
 }
 
-// Counts every kernel launch made through the library (for the launch census).
-extern int64_t g_launches;
+// Counts every kernel launch made through the library (for the launch census);
+// atomic because plans may run concurrently from several host threads.
+extern std::atomic<int64_t> g_launches;
+// Launches made by the calling host thread (per-plan counts are differences of it).
+extern thread_local int64_t t_launches;
+inline void note_launch(int64_t n = 1) {
+  g_launches += n;
+  t_launches += n;
+}
 
 }  // namespace kfm

@@ -5,7 +5,8 @@
 
 namespace kfm {
 
-int64_t g_launches = 0;
+std::atomic<int64_t> g_launches{0};
+thread_local int64_t t_launches = 0;
 
 template <typename T> struct SimtCfg;
 // float64: 64 x 64 tiles, 4 x 4 outputs per thread (the FP64 pipe is the limit).
@@ -135,7 +136,7 @@ kf_status gemm_simt(cudaStream_t s, bool transB, const GemmParams<T>& p) {
     gemm_simt_kernel<T, true><<<grid, 256, 0, s>>>(p);
   else
     gemm_simt_kernel<T, false><<<grid, 256, 0, s>>>(p);
-  ++g_launches;
+  note_launch();
   return launch_check("gemm_simt");
 }
 

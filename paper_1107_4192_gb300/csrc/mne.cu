@@ -69,7 +69,7 @@ extern "C" kf_status mne_solve(const double* H, const double* C, int32_t c_kind,
     KF_CUDA_TRY(cudaMemcpyAsync(HC, H, (size_t)m * N * 8, cudaMemcpyDeviceToDevice, s));
     dim3 grid((unsigned)std::min<int64_t>(ceil_div(N, 256), 64), (unsigned)std::min<int64_t>(m, 65535));
     scale_cols_kernel<<<grid, 256, 0, s>>>(m, N, HC, N, c_kind, C, 1.0);
-    ++g_launches;
+    note_launch();
     KF_TRY(launch_check("scale_cols"));
   }
   // G = lambda (H C) H^T + R, symmetric by construction

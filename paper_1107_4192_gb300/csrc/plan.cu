@@ -80,7 +80,7 @@ struct kf_plan_s {
   bool prof = false;
   std::vector<ProfMark> marks;
   std::vector<cudaEvent_t> pool;
-  int64_t launches0 = 0;
+  int64_t launches = 0;  // kernels launched by this plan's calls
 
   // Store slots: every P_{t|t} when ckpt == 1; otherwise checkpoints at
   // t = 0, c, 2c, .., a permanent slot for t = 1 (see filter_first_fp64) and a
@@ -652,7 +652,7 @@ kf_status chol_inverse_step(kf_plan_s* p, float* Lb, int step) {
       p->cap_stream = nullptr;
       return KF_OK;
     }
-    const int64_t l0 = g_launches;
+    const int64_t l0 = t_launches;
     cudaGraph_t graph = nullptr;
     if (cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
       cudaGetLastError();
@@ -663,11 +663,12 @@ kf_status chol_inverse_step(kf_plan_s* p, float* Lb, int step) {
     cudaError_t e = cudaStreamEndCapture(p->cap_stream, &graph);
     if (st == KF_OK && e == cudaSuccess && graph &&
         cudaGraphInstantiate(&p->chol_graph, graph, 0) == cudaSuccess) {
-      p->graph_launches = g_launches - l0;
+      p->graph_launches = t_launches - l0;
     } else {
       p->chol_graph = nullptr;
     }
-    g_launches = l0;
+    g_launches -= t_launches - l0;  // the capture launched nothing
+    t_launches = l0;
     if (graph) cudaGraphDestroy(graph);
     cudaGetLastError();
     return KF_OK;
@@ -676,7 +677,7 @@ kf_status chol_inverse_step(kf_plan_s* p, float* Lb, int step) {
     return chol_inverse_tc(p->s, p->tc, N, Lb, p->ldN, p->Wi, p->ldN, (float*)p->tmpN, p->ldN, p->status, step);
   KF_TRY(set_status_step(p->s, p->status, step));
   KF_CUDA_TRY(cudaGraphLaunch(p->chol_graph, p->s));
-  g_launches += p->graph_launches;
+  note_launch(p->graph_launches);
   return KF_OK;
 }
 
@@ -869,7 +870,6 @@ kf_status kf_plan(kf_plan_t* out, const kf_desc* d) {
   p->smooth_slices = d->split_terms == 6 ? 3 : 2;
   p->slot = z.slot;
   p->ckpt = c;
-  p->launches0 = g_launches;
   const int64_t N = p->N, m = p->m, T = p->T, ldN = p->ldN, ldm = p->ldm;
   const size_t b = p->b, sb = p->sb;
   kf_status st = KF_OK;
@@ -946,9 +946,12 @@ kf_status kf_filter(kf_plan_t p, const double* F, const int64_t* F_rowptr, const
   if (p->d.f_kind != KF_F_IDENTITY && !F) return KF_ERR_ARG;
   if (p->d.f_kind == KF_F_CSR && (!F_rowptr || !F_col)) return KF_ERR_ARG;
   p->filtered = false;
-  KF_TRY(copy_inputs(p, F, F_rowptr, F_col, Q, H, R));
-  kf_status st = p->b == 8 ? run_filter<double>(p, Y, x0, P0, x_filt, diagP_filt, fail_step)
-                           : run_filter<float>(p, Y, x0, P0, x_filt, diagP_filt, fail_step);
+  const int64_t l0 = t_launches;
+  kf_status st = copy_inputs(p, F, F_rowptr, F_col, Q, H, R);
+  if (st == KF_OK)
+    st = p->b == 8 ? run_filter<double>(p, Y, x0, P0, x_filt, diagP_filt, fail_step)
+                   : run_filter<float>(p, Y, x0, P0, x_filt, diagP_filt, fail_step);
+  p->launches += t_launches - l0;
   p->filtered = st == KF_OK;
   return st;
 }
@@ -959,9 +962,16 @@ kf_status fis_smooth(kf_plan_t p, double* x_smooth, double* diagP_smooth, double
   if (!p || !x_smooth) return KF_ERR_ARG;
   if (P_smooth_at && (t_full < 1 || t_full > p->T)) return KF_ERR_ARG;
   if (!p->filtered) return KF_ERR_STATE;
-  if (p->b == 8) return run_smoother<double, double>(p, x_smooth, diagP_smooth, P_smooth_at, t_full, fail_step);
-  if (p->sb == 8) return run_smoother<float, double>(p, x_smooth, diagP_smooth, P_smooth_at, t_full, fail_step);
-  return run_smoother<float, float>(p, x_smooth, diagP_smooth, P_smooth_at, t_full, fail_step);
+  const int64_t l0 = t_launches;
+  kf_status st;
+  if (p->b == 8)
+    st = run_smoother<double, double>(p, x_smooth, diagP_smooth, P_smooth_at, t_full, fail_step);
+  else if (p->sb == 8)
+    st = run_smoother<float, double>(p, x_smooth, diagP_smooth, P_smooth_at, t_full, fail_step);
+  else
+    st = run_smoother<float, float>(p, x_smooth, diagP_smooth, P_smooth_at, t_full, fail_step);
+  p->launches += t_launches - l0;
+  return st;
 }
 
 kf_status kf_solve_host(kf_plan_t p, const double* F, const int64_t* F_rowptr, const int64_t* F_col,
@@ -1054,7 +1064,7 @@ kf_status kf_plan_profile_read(kf_plan_t p, int32_t cls, int64_t* launches, doub
   return KF_OK;
 }
 
-int64_t kf_plan_launch_count(kf_plan_t p) { return p ? g_launches - p->launches0 : 0; }
+int64_t kf_plan_launch_count(kf_plan_t p) { return p ? p->launches : 0; }
 
 void kf_plan_destroy(kf_plan_t p) {
   if (!p) return;

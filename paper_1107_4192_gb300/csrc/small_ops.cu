@@ -28,7 +28,7 @@ kf_status copy2d(cudaStream_t s, Tdst* dst, int64_t ldd, const Tsrc* src, int64_
   int64_t pad_to = zero_pad ? ldd : cols;
   dim3 grid((unsigned)std::min<int64_t>(ceil_div(pad_to, 256), 64), (unsigned)std::min<int64_t>(rows, 65535));
   copy2d_kernel<Tdst, Tsrc><<<grid, 256, 0, s>>>(dst, ldd, src, lds, rows, cols, pad_to);
-  ++g_launches;
+  note_launch();
   return launch_check("copy2d");
 }
 
@@ -46,7 +46,7 @@ kf_status add_cov(cudaStream_t s, Tdst* dst, int64_t ldd, const Tsrc* src, int64
   if (n <= 0) return KF_OK;
   dim3 grid((unsigned)std::min<int64_t>(ceil_div(n, 256), 64), (unsigned)std::min<int64_t>(n, 65535));
   add_cov_kernel<Tdst, Tsrc><<<grid, 256, 0, s>>>(dst, ldd, src, lds, n, q_kind, q);
-  ++g_launches;
+  note_launch();
   return launch_check("add_cov");
 }
 
@@ -72,7 +72,7 @@ kf_status gemv(cudaStream_t s, int64_t rows, int64_t cols, const T* A, int64_t l
   if (rows <= 0) return KF_OK;
   unsigned blocks = (unsigned)std::min<int64_t>(ceil_div(rows * 32, 256), 4096);
   gemv_kernel<T><<<blocks, 256, 0, s>>>(rows, cols, A, lda, x, ybase, sign, y);
-  ++g_launches;
+  note_launch();
   return launch_check("gemv");
 }
 
@@ -80,7 +80,7 @@ __global__ void set_step_kernel(int* status, int step) { status[ST_CUR] = step; 
 
 kf_status set_status_step(cudaStream_t s, int* status, int step) {
   set_step_kernel<<<1, 1, 0, s>>>(status, step);
-  ++g_launches;
+  note_launch();
   return launch_check("set_step");
 }
 
@@ -92,7 +92,7 @@ __global__ void vsub_kernel(int64_t n, const double* a, const double* b, double*
 kf_status vsub(cudaStream_t s, int64_t n, const double* a, const double* b, double* d) {
   if (n <= 0) return KF_OK;
   vsub_kernel<<<(unsigned)std::min<int64_t>(ceil_div(n, 256), 1024), 256, 0, s>>>(n, a, b, d);
-  ++g_launches;
+  note_launch();
   return launch_check("vsub");
 }
 
@@ -118,7 +118,7 @@ kf_status innovation(cudaStream_t s, int64_t m, int64_t N, const double* H, cons
                      const double* y, double* nu, int* status, int step) {
   unsigned blocks = (unsigned)std::min<int64_t>(ceil_div(m * 32, 256), 1024);
   innovation_kernel<<<blocks, 256, 0, s>>>(m, N, H, x, y, nu, status, step);
-  ++g_launches;
+  note_launch();
   return launch_check("innovation");
 }
 
@@ -189,11 +189,11 @@ kf_status innovation_cov(cudaStream_t s, int m, int N, const double* H, int64_t 
   int used = (int)ceil_div(N, chunk);
   dim3 grid((unsigned)ceil_div(m, 32), (unsigned)ceil_div(m, 32), (unsigned)used);
   innov_cov_partial_kernel<T><<<grid, 256, 0, s>>>(m, N, H, ldh, Ut, ldu, partials, chunk);
-  ++g_launches;
+  note_launch();
   KF_TRY(launch_check("innov_cov_partial"));
   unsigned blocks = (unsigned)std::min<int64_t>(ceil_div((int64_t)m * m, 256), 1024);
   innov_cov_reduce_kernel<<<blocks, 256, 0, s>>>(m, partials, used, r_kind, R, S, lds);
-  ++g_launches;
+  note_launch();
   return launch_check("innov_cov_reduce");
 }
 
@@ -214,7 +214,7 @@ kf_status predict_mean(cudaStream_t s, int f_kind, int64_t N, const double* F, c
   }
   if (f_kind == KF_F_CSR) {
     spmv_kernel<<<(unsigned)std::min<int64_t>(ceil_div(N, 256), 1024), 256, 0, s>>>(N, rowptr, col, F, x, x_out);
-    ++g_launches;
+    note_launch();
     return launch_check("spmv");
   }
   return gemv<double>(s, N, N, F, N, x, nullptr, 1.0, x_out);
@@ -244,7 +244,7 @@ kf_status split_bf16(cudaStream_t s, int64_t rows, int64_t cols, const float* A,
   Planes3 pl{{planes[0], n > 1 ? planes[1] : nullptr, n > 2 ? planes[2] : nullptr}};
   dim3 grid((unsigned)std::min<int64_t>(ceil_div(ldh, 256), 64), (unsigned)std::min<int64_t>(rows, 65535));
   split_bf16_kernel<<<grid, 256, 0, s>>>(rows, cols, A, lda, pl, n, ldh);
-  ++g_launches;
+  note_launch();
   return launch_check("split_bf16");
 }
 
@@ -279,7 +279,7 @@ kf_status split_bf16_t(cudaStream_t s, int64_t rows, int64_t cols, const float* 
   Planes3 pl{{planes[0], n > 1 ? planes[1] : nullptr, n > 2 ? planes[2] : nullptr}};
   dim3 grid((unsigned)ceil_div(rows, 32), (unsigned)ceil_div(ldh, 32));
   split_bf16_t_kernel<<<grid, 256, 0, s>>>(rows, cols, A, lda, pl, n, ldh);
-  ++g_launches;
+  note_launch();
   return launch_check("split_bf16_t");
 }
 
@@ -344,7 +344,7 @@ kf_status split_bf16_pair(cudaStream_t s, const SplitOp& a, const SplitOp& b, in
   if (ceil_div(rows, 32) > 0x7fffffff || ceil_div(ldh, 32) > 65535) return KF_ERR_ARG;
   dim3 grid((unsigned)ceil_div(rows, 32), (unsigned)ceil_div(ldh, 32), 2);
   split_bf16_pair_kernel<<<grid, 256, 0, s>>>(a, b, n, ldh);
-  ++g_launches;
+  note_launch();
   return launch_check("split_bf16_pair");
 }
 
@@ -358,7 +358,7 @@ template <typename T>
 kf_status diag_extract(cudaStream_t s, int64_t n, const T* A, int64_t lda, double* diag_out) {
   if (n <= 0) return KF_OK;
   diag_kernel<T><<<(unsigned)std::min<int64_t>(ceil_div(n, 256), 1024), 256, 0, s>>>(n, A, lda, diag_out);
-  ++g_launches;
+  note_launch();
   return launch_check("diag");
 }
 

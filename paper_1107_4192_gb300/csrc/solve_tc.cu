@@ -159,7 +159,7 @@ kf_status gain_identity_tc(cudaStream_t s, TcScratch& sc, int n, const float* W,
   KF_TRY(tc_gemm_ops(s, sc, TcOperand{W, ldw, 0, 1}, TcOperand{W, ldw, 0, 1}, g, 3));
   dim3 grid((unsigned)std::min<int64_t>(ceil_div(n, 256), 64), (unsigned)std::min<int64_t>(n, 65535));
   gain_identity_kernel<<<grid, 256, 0, s>>>(n, Pinv, ldp, q_kind, q, J, ldj);
-  ++g_launches;
+  note_launch();
   return launch_check("gain_identity");
 }
 

@@ -44,10 +44,10 @@ kf_status spmm_fpft(cudaStream_t s, int64_t N, const int64_t* rowptr, const int6
   if (N <= 0) return KF_OK;
   unsigned blocks = (unsigned)std::min<int64_t>(N, 1 << 20);
   spmm_fp_kernel<T><<<blocks, 256, 0, s>>>(N, rowptr, col, val, P, ldp, W, ldw);
-  ++g_launches;
+  note_launch();
   KF_TRY(launch_check("spmm_fp"));
   spmm_wft_kernel<T><<<blocks, 256, 0, s>>>(N, rowptr, col, val, W, ldw, out, ldo, q_kind, q);
-  ++g_launches;
+  note_launch();
   return launch_check("spmm_wft");
 }
 
@@ -57,7 +57,7 @@ kf_status spmm_pft(cudaStream_t s, int64_t N, const int64_t* rowptr, const int64
   if (N <= 0) return KF_OK;
   unsigned blocks = (unsigned)std::min<int64_t>(N, 1 << 20);
   spmm_wft_kernel<T><<<blocks, 256, 0, s>>>(N, rowptr, col, val, P, ldp, out, ldo, -1, nullptr);
-  ++g_launches;
+  note_launch();
   return launch_check("spmm_pft");
 }
 

@@ -382,18 +382,18 @@ kf_status launch(cudaStream_t s, const GemmParams<TE>& g, const TcScratch& sc, i
     KF_TRY(make_map(&maps.a[i], sc.a[i], g.M, ldk, ldk, BM));
     KF_TRY(make_map(&maps.b[i], sc.b[i], g.N, ldk, ldk, BN));
   }
-  static bool configured = false;
-  if (!configured) {
-    KF_CUDA_TRY(
-        cudaFuncSetAttribute(tc_gemm_kernel<BN, S, TE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
-    configured = true;
-  }
+  static std::once_flag configured;
+  static cudaError_t cfg_err = cudaSuccess;
+  std::call_once(configured, [&] {
+    cfg_err = cudaFuncSetAttribute(tc_gemm_kernel<BN, S, TE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+  });
+  KF_CUDA_TRY(cfg_err);
   dim3 grid((unsigned)ceil_div(g.N, BN), (unsigned)ceil_div(g.M, BM));
   const int num_k_tiles = (int)(ldk / BK);
   if (g_tc_timer) g_tc_timer->before(s);
   tc_gemm_kernel<BN, S, TE><<<grid, NUM_THREADS, C::SMEM, s>>>(maps, g, num_k_tiles);
   if (g_tc_timer) g_tc_timer->after(s);
-  ++g_launches;
+  note_launch();
   return launch_check("tc_gemm");
 }
 

@@ -1,0 +1,223 @@
+"""Continuous-batching server for filter + smoother requests (epochs).
+
+Requests (MEG epochs of different N, m, T) arrive over time.  The scheduler
+admits a waiting request as soon as a slot is free and its device footprint
+fits the memory budget, then runs it on its own CUDA stream from a worker
+thread, so the kernels of concurrently admitted epochs overlap on the GPU.
+Each admitted epoch keeps its filter state and covariance store on the device
+for the whole request.
+
+Admission charges a request 2 N^2 T 4 bytes (predicted and filtered float32
+covariances for every step) plus the plan's workspace.  When that does not
+fit but the plan can run within the free memory by keeping only checkpoints
+of P_{t|t} and recomputing the rest forward during the smoother, the request
+is admitted in that mode, charged what its plan actually allocates.  A request
+that cannot fit even so into the whole budget is rejected.
+
+Every epoch's computation is independent of the others (own plan, own
+stream, deterministic kernels), so a result is bitwise the same alone and in
+the mix.
+
+Only marshalling and scheduling happen here; all arithmetic runs in the
+library's CUDA kernels.
+"""
+from __future__ import annotations
+
+import threading
+import time
+from dataclasses import dataclass, field
+from typing import Dict, List, Optional
+
+import numpy as np
+
+from . import binding as B
+from . import solver
+
+
+@dataclass
+class Request:
+    rid: int
+    arrival_s: float
+    problem: object                     # synth.Problem (inputs arrive with the request)
+    prec: int = B.KF_PREC_MIXED_BF16X3
+    solve_prec: int = B.KF_SOLVE_FP32
+    joseph_every: int = 16
+
+
+@dataclass
+class Result:
+    rid: int
+    N: int
+    m: int
+    T: int
+    arrival_s: float
+    admitted_s: float = 0.0
+    finished_s: float = 0.0
+    charged_bytes: int = 0
+    checkpoint_every: int = 1
+    status: str = "ok"
+    outputs: Optional[Dict[str, np.ndarray]] = None
+
+    @property
+    def latency_s(self):
+        return self.finished_s - self.arrival_s
+
+    @property
+    def queue_s(self):
+        return self.admitted_s - self.arrival_s
+
+
+def admission_footprint(N: int, T: int) -> int:
+    """2 N^2 T float32 words: the admission rule for one epoch."""
+    return 2 * N * N * T * 4
+
+
+def input_bytes(prob) -> int:
+    """Device bytes of one request's float64 inputs (P0 dense, H, Y, x0, F, Q, R)."""
+    N, m, T = prob.N, prob.m, prob.T
+    b = 8 * (N * N + m * N + T * m + N)
+    if prob.F is not None:
+        b += 16 * prob.F.nnz + 8 * (N + 1)
+    b += 8 * (1 if prob.q_kind == 0 else N if prob.q_kind == 1 else N * N)
+    b += 8 * (1 if prob.r_kind == 0 else m if prob.r_kind == 1 else m * m)
+    return b
+
+
+def plan_bytes(prob, req: Request, budget: int):
+    """(status, bytes, checkpoint_every) of the plan this request would allocate within `budget`."""
+    h = solver.host_inputs(prob)
+    d = B.make_desc(prob.N, prob.m, prob.T, h["f_kind"], req.prec, req.solve_prec, h["q_kind"], h["r_kind"],
+                    req.joseph_every, h["f_nnz"], budget, 0, 0, 0)
+    st, w, s, c = B.kf_plan_footprint(d)
+    return st, w + s, c
+
+
+class Server:
+    """Admits requests as slots and memory free up; runs each on its own stream."""
+
+    def __init__(self, budget_bytes: int = 160 * 10 ** 9, max_slots: int = 4, keep_outputs: bool = False,
+                 device: str = "cuda"):
+        self.budget = int(budget_bytes)
+        self.max_slots = max_slots
+        self.keep_outputs = keep_outputs
+        self.device = device
+        self._lock = threading.Lock()
+        self._cv = threading.Condition(self._lock)
+        self._in_use = 0
+        self._active = 0
+
+    def _charge(self, prob, req):
+        """(bytes to reserve now, plan budget): bytes None = wait, -1 = never fits."""
+        inputs = input_bytes(prob)
+        free = self.budget - self._in_use - inputs
+        need_full = admission_footprint(prob.N, prob.T)
+        st, full_bytes, c = plan_bytes(prob, req, 0)
+        if max(need_full, full_bytes) <= free:
+            return max(need_full, full_bytes) + inputs, 0
+        if free > 0:
+            st, ck_bytes, c = plan_bytes(prob, req, free)
+            if st == B.KF_OK:
+                return ck_bytes + inputs, free
+        st, _, _ = plan_bytes(prob, req, self.budget - inputs)
+        return (-1, 0) if st != B.KF_OK else (None, 0)
+
+    def _worker(self, req: Request, res: Result, budget: int, t0: float):
+        import torch
+        prob = req.problem
+        try:
+            stream = torch.cuda.Stream()
+            with torch.cuda.stream(stream):
+                d = solver.upload(prob, self.device)
+                plan = solver.Plan.for_inputs(d, prob.N, prob.m, prob.T, prec=req.prec, solve_prec=req.solve_prec,
+                                              joseph_every=req.joseph_every, mem_budget_bytes=budget,
+                                              stream=stream.cuda_stream)
+                try:
+                    res.checkpoint_every = B.kf_plan_footprint(plan.desc)[3]
+                    xf, df = plan.filter(d)
+                    xs, ds, _ = plan.smooth()
+                    out = {"x_filt": xf.cpu().numpy(), "diagP_filt": df.cpu().numpy(),
+                           "x_smooth": xs.cpu().numpy(), "diagP_smooth": ds.cpu().numpy()}
+                    if self.keep_outputs:
+                        res.outputs = out
+                finally:
+                    plan.close()
+                stream.synchronize()
+        except Exception as e:  # reported per request; the server keeps serving
+            res.status = f"error: {e}"
+        res.finished_s = time.perf_counter() - t0
+        with self._cv:
+            self._in_use -= res.charged_bytes
+            self._active -= 1
+            self._cv.notify_all()
+
+    def run(self, requests: List[Request], time_scale: float = 1.0) -> List[Result]:
+        """Serves requests arriving at arrival_s * time_scale seconds after the start."""
+        reqs = sorted(requests, key=lambda r: r.arrival_s)
+        results = {r.rid: Result(r.rid, r.problem.N, r.problem.m, r.problem.T, r.arrival_s * time_scale)
+                   for r in reqs}
+        threads = []
+        t0 = time.perf_counter()
+        pending: List[Request] = []
+        i = 0
+        with self._cv:
+            while i < len(reqs) or pending:
+                now = time.perf_counter() - t0
+                while i < len(reqs) and reqs[i].arrival_s * time_scale <= now:
+                    pending.append(reqs[i])
+                    i += 1
+                admitted_any = False
+                for req in list(pending):          # first come, first served, skipping what does not fit
+                    if self._active >= self.max_slots:
+                        break
+                    charge, budget = self._charge(req.problem, req)
+                    if charge is None:
+                        continue
+                    pending.remove(req)
+                    res = results[req.rid]
+                    if charge < 0:
+                        res.status = "rejected: does not fit the memory budget"
+                        res.admitted_s = res.finished_s = now
+                        continue
+                    res.charged_bytes = charge
+                    res.admitted_s = now
+                    self._in_use += charge
+                    self._active += 1
+                    th = threading.Thread(target=self._worker, args=(req, res, budget, t0), daemon=True)
+                    threads.append(th)
+                    th.start()
+                    admitted_any = True
+                if admitted_any:
+                    continue
+                next_arrival = reqs[i].arrival_s * time_scale - now if i < len(reqs) else None
+                timeout = 0.05 if next_arrival is None else max(0.0, min(next_arrival, 0.05))
+                self._cv.wait(timeout=timeout)
+        for th in threads:
+            th.join()
+        return [results[r.rid] for r in reqs]
+
+
+def summarize(results: List[Result], wall_s: Optional[float] = None) -> dict:
+    ok = [r for r in results if r.status == "ok"]
+    lat = np.array([r.latency_s for r in ok]) if ok else np.zeros(1)
+    steps = sum(r.T for r in ok)
+    wall = wall_s if wall_s is not None else (max(r.finished_s for r in ok) - min(r.arrival_s for r in results)
+                                              if ok else 0.0)
+    return {"requests": len(results), "completed": len(ok),
+            "rejected": sum(r.status.startswith("rejected") for r in results),
+            "errors": sum(r.status.startswith("error") for r in results),
+            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+            "mean_queue_s": float(np.mean([r.queue_s for r in ok])) if ok else 0.0,
+            "timesteps": int(steps), "wall_s": float(wall),
+            "timesteps_per_s": float(steps / wall) if wall > 0 else 0.0,
+            "recompute_requests": sum(r.checkpoint_every > 1 for r in ok)}
+
+
+def run_batch(problems, max_slots: int = 8, budget_bytes: int = 160 * 10 ** 9, prec=B.KF_PREC_MIXED_BF16X3,
+              solve_prec=B.KF_SOLVE_FP32, keep_outputs: bool = False):
+    """Many uneven epochs at once: all arrive at t = 0 and run concurrently, max_slots at a time."""
+    reqs = [Request(i, 0.0, p, prec=prec, solve_prec=solve_prec) for i, p in enumerate(problems)]
+    server = Server(budget_bytes, max_slots, keep_outputs)
+    t0 = time.perf_counter()
+    res = server.run(reqs)
+    wall = time.perf_counter() - t0
+    return res, summarize(res, wall)

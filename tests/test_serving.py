@@ -1,0 +1,81 @@
+"""Continuous-batching server: admission by footprint (host logic, CPU) and
+identical results alone and in the mix (GPU)."""
+import numpy as np
+import pytest
+
+from paper_1107_4192_gb300 import binding as B
+from paper_1107_4192_gb300 import serve, synth
+
+
+@pytest.fixture(scope="module")
+def built():
+    from paper_1107_4192_gb300 import build
+    build.build()
+    B.lib()
+
+
+def test_admission_footprint_rule():
+    assert serve.admission_footprint(8196, 400) == 2 * 8196 ** 2 * 400 * 4
+    assert serve.admission_footprint(8196, 400) > 160e9  # must run in recompute mode
+    assert serve.admission_footprint(1024, 50) < 1e9
+
+
+def test_charge_full_checkpointed_and_rejected(built):
+    prob = synth.random_walk_problem(512, 32, 40, seed=1)
+    req = serve.Request(0, 0.0, prob)
+    st, full, c = serve.plan_bytes(prob, req, 0)
+    assert st == 0 and c == 1
+    srv = serve.Server(budget_bytes=10 * full, max_slots=2)
+    charge, budget = srv._charge(prob, req)
+    assert charge >= full and budget == 0                      # full store fits
+    srv = serve.Server(budget_bytes=int(0.7 * full) + serve.input_bytes(prob), max_slots=2)
+    charge, budget = srv._charge(prob, req)
+    assert charge is not None and charge > 0 and budget > 0    # admitted with checkpoints
+    assert serve.plan_bytes(prob, req, budget)[2] > 1
+    srv = serve.Server(budget_bytes=serve.input_bytes(prob) + 1000, max_slots=2)
+    assert srv._charge(prob, req)[0] == -1                      # can never fit
+
+
+def _requests(prec):
+    probs = [synth.random_walk_problem(256, 32, 7, seed=1), synth.mesh_problem(324, 40, 6, seed=2),
+             synth.random_walk_problem(384, 64, 9, seed=3), synth.mesh_problem(200, 20, 5, seed=4)]
+    return [serve.Request(i, 0.01 * i, p, prec=prec, solve_prec=B.KF_SOLVE_FP32, joseph_every=4)
+            for i, p in enumerate(probs)]
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", [B.KF_PREC_MIXED_BF16X3, B.KF_PREC_FP64])
+def test_alone_equals_mix(built, prec):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    alone = serve.Server(max_slots=1, keep_outputs=True).run(_requests(prec))
+    mix = serve.Server(max_slots=4, keep_outputs=True).run(_requests(prec))
+    for a, b in zip(alone, mix):
+        assert a.status == b.status == "ok"
+        for k in a.outputs:
+            assert np.array_equal(a.outputs[k], b.outputs[k]), (a.rid, k)
+
+
+@pytest.mark.gpu
+def test_recompute_mode_under_a_small_budget(built):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    probs = [synth.mesh_problem(324, 40, 12, seed=5), synth.random_walk_problem(256, 32, 10, seed=6)]
+    reqs = [serve.Request(i, 0.0, p, prec=B.KF_PREC_FP64) for i, p in enumerate(probs)]
+    full = serve.Server(max_slots=2, keep_outputs=True).run(reqs)
+    st, fb, _ = serve.plan_bytes(probs[0], reqs[0], 0)
+    # the largest budget (in 2% steps below the full footprint) that forces checkpointing
+    budget = next(int(f * fb) for f in np.arange(0.98, 0.3, -0.02)
+                  if serve.plan_bytes(probs[0], reqs[0], int(f * fb))[0] == 0
+                  and serve.plan_bytes(probs[0], reqs[0], int(f * fb))[2] > 1)
+    tight = serve.Server(budget_bytes=budget + serve.input_bytes(probs[0]), max_slots=2,
+                         keep_outputs=True).run(reqs)
+    assert tight[0].checkpoint_every > 1
+    for a, b in zip(full, tight):
+        assert b.status == "ok"
+        for k in a.outputs:  # float64 recomputation repeats the forward pass exactly
+            assert np.array_equal(a.outputs[k], b.outputs[k]), k
+    s = serve.summarize(tight)
+    assert s["completed"] == 2 and s["recompute_requests"] >= 1
