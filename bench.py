@@ -125,6 +125,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-plain", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--serve-requests", type=int, default=12,
+                    help="requests of the Poisson serving stream to replay (0 = skip)")
+    ap.add_argument("--batch-epochs", type=int, default=64, help="uneven epochs of the batched workload (0 = skip)")
     return ap.parse_args()
 
 
@@ -316,6 +319,10 @@ def main():
                     "d2h_bytes_per_step": d2h},
             "phase_ms": {names[c]: prof[c][1] / args.steps for c in prof}}
 
+    if rank == 0 and world == 1 and args.batch_epochs > 0:
+        line["batched"] = batched_sample(args, B, synth)
+    if rank == 0 and world == 1 and args.serve_requests > 0:
+        line["serve"] = serving_sample(args, B, synth)
     if rank == 0 and world == 1 and not args.no_fp64_plain and args.prec != "fp64":
         line["fp64_plain"] = fp64_plain_prefix(prob, B, solver, synth, torch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -326,6 +333,33 @@ def main():
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def serving_sample(args, B, synth):
+    """The first requests of the seeded Poisson stream (20 req/s; N in {1024, 2048, 5124, 8196},
+    m = 306, T ~ U{50..400}), served with admission by footprint against 160 GB."""
+    from paper_1107_4192_gb300 import serve
+    arrivals = synth.serving_arrivals(2000, 20.0, seed=4)[:args.serve_requests]
+    reqs = []
+    for i, (t, N, m, T) in enumerate(arrivals):
+        prob = synth.mesh_problem(N, m, T, seed=4000 + i, identity_F=(i % 2 == 0))
+        reqs.append(serve.Request(i, t, prob))
+    res = serve.Server(160 * 10 ** 9, max_slots=4).run(reqs)
+    out = serve.summarize(res)
+    out["sample"] = (f"first {len(reqs)} requests of the 2000-request stream (arrivals over "
+                     f"{arrivals[-1][0]:.2f} s), mixed path, 4 slots")
+    return out
+
+
+def batched_sample(args, B, synth):
+    """Uneven epochs (N ~ U{256..2048 step 128}, m in {64,128,306}, T ~ U{20..200}, F = I or mesh)
+    all submitted at once and run concurrently, 8 at a time."""
+    from paper_1107_4192_gb300 import serve
+    probs = synth.batched_epochs(args.batch_epochs, seed=3)
+    _, summ = serve.run_batch(probs, max_slots=8)
+    summ["epochs_per_s"] = summ["completed"] / summ["wall_s"] if summ["wall_s"] > 0 else 0.0
+    summ["sample"] = f"{len(probs)} epochs, 8 concurrent plans on separate streams"
+    return summ
 
 
 def fp64_plain_prefix(prob, B, solver, synth, torch, T_pre=3):

@@ -23,6 +23,7 @@ from __future__ import annotations
 
 from collections import deque
 from dataclasses import dataclass, field
+from functools import lru_cache
 from typing import Optional
 
 import numpy as np
@@ -106,8 +107,17 @@ def sphere_for(n_vertices: int):
     return fibonacci_sphere(n_vertices)
 
 
+@lru_cache(maxsize=16)
+def _hemisphere_mesh_cached(N: int):
+    return tuple(tuple(s) for s in _hemisphere_mesh(N))
+
+
 def hemisphere_mesh(N: int):
     """Neighbour lists for N sources split over two hemispheres (blocks)."""
+    return [list(s) for s in _hemisphere_mesh_cached(N)]
+
+
+def _hemisphere_mesh(N: int):
     halves = [N // 2, N - N // 2] if N >= 8 else [N]
     neigh, off = [], 0
     for h in halves:
