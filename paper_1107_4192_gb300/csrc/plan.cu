@@ -127,7 +127,8 @@ Sizes sizes_for(const kf_desc* d) {
   if (d->f_kind == KF_F_CSR) w += d->f_nnz * 16 + (N + 1) * 8;
   if (d->f_kind == KF_F_DENSE) w += N * N * 8 + z.slot;
   w += cov_count(d->q_kind, N) * 8 + m * N * 8 + cov_count(d->r_kind, m) * 8;
-  if (d->prec == KF_PREC_MIXED_BF16X3) w += tc_scratch_bytes(N, ldN);
+  // split planes: rows up to max(N, m), k up to max(ldN, 2 ldm) (the Joseph product's rank 2m)
+  if (d->prec == KF_PREC_MIXED_BF16X3) w += tc_scratch_bytes(std::max(N, m), std::max(ldN, 2 * ldm));
   w += 4096;
   z.workspace = w;
   return z;
@@ -925,7 +926,7 @@ kf_status kf_plan(kf_plan_t* out, const kf_desc* d) {
   A(&p->H, m * N * 8);
   A(&p->R, cov_count(d->r_kind, m) * 8);
   A(&p->status, ST_WORDS * sizeof(int));
-  if (st == KF_OK && p->bulk == BULK_BF16X3) st = tc_scratch_alloc(p->tc, N, ldN, [&](void** ptr, size_t bytes) {
+  if (st == KF_OK && p->bulk == BULK_BF16X3) st = tc_scratch_alloc(p->tc, std::max(N, m), std::max(ldN, 2 * ldm), [&](void** ptr, size_t bytes) {
     return dalloc(p, (char**)ptr, bytes);
   });
   if (st == KF_OK && cudaMallocHost(&p->status_h, ST_WORDS * sizeof(int)) != cudaSuccess) st = KF_ERR_CUDA;

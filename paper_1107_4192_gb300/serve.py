@@ -209,7 +209,8 @@ def summarize(results: List[Result], wall_s: Optional[float] = None) -> dict:
             "mean_queue_s": float(np.mean([r.queue_s for r in ok])) if ok else 0.0,
             "timesteps": int(steps), "wall_s": float(wall),
             "timesteps_per_s": float(steps / wall) if wall > 0 else 0.0,
-            "recompute_requests": sum(r.checkpoint_every > 1 for r in ok)}
+            "recompute_requests": sum(r.checkpoint_every > 1 for r in ok),
+            "error_messages": sorted({r.status for r in results if r.status.startswith("error")})[:4]}
 
 
 def run_batch(problems, max_slots: int = 8, budget_bytes: int = 160 * 10 ** 9, prec=B.KF_PREC_MIXED_BF16X3,

@@ -75,7 +75,7 @@ def test_mixed_bf16x3_paths(solve, mesh):
     check(out, run_oracle(prob), TOL_MEAN32, TOL_DIAG32)
 
 
-@pytest.mark.parametrize("N,m,T", [(129, 20, 4), (257, 70, 5), (600, 64, 4)])
+@pytest.mark.parametrize("N,m,T", [(129, 20, 4), (257, 70, 5), (600, 64, 4), (200, 306, 5), (512, 306, 6)])
 def test_mixed_ragged_sizes(N, m, T):
     prob = synth.random_walk_problem(N, m, T, seed=N + m)
     out = solver.run(prob, prec=B.KF_PREC_MIXED_BF16X3, solve_prec=B.KF_SOLVE_FP32, joseph_every=2)
