@@ -218,3 +218,24 @@ def test_tc_bf16x6_gemm(transB, M, N, K):
     assert np.abs(got - exact).max() <= 4e-6 * max(1.0, np.sqrt(K)) * np.abs(exact).max()
     full = A.astype(np.float64) @ Bnk.astype(np.float64).T
     assert np.linalg.norm(got - full) <= 1e-5 * np.linalg.norm(full)
+
+
+@pytest.mark.parametrize("dtype", [2, 3])
+def test_tc_accumulation_bias(dtype):
+    """Same-sign data, K = 8192: the tensor cores' float32 accumulation truncates, so the kernel
+    promotes partial sums to float32 registers every k-tile.  The relative bias must stay small and
+    independent of K (without promotion it grew to about -4.5e-5 at this K)."""
+    rng = np.random.default_rng(0)
+    rows = []
+    for K in (512, 8192):
+        A = rng.random((256, K)).astype(np.float32)
+        Bm = rng.random((256, K)).astype(np.float32)
+        ref = A.astype(np.float64) @ Bm.astype(np.float64).T
+        dC = torch.zeros(256, 256, dtype=torch.float32, device="cuda")
+        B.kfx_gemm(dtype, 1, 0, 256, 256, K, 1.0, torch.from_numpy(A).cuda(), K, torch.from_numpy(Bm).cuda(), K,
+                   0.0, dC, 256)
+        e = (dC.double().cpu().numpy() - ref) / ref
+        rows.append((K, float(e.mean()), float(np.abs(e).max())))
+        print(f"dtype {dtype} K {K}: mean relative error {e.mean():+.2e}, max {np.abs(e).max():.2e}")
+    for K, mean, mx in rows:
+        assert abs(mean) < 1e-6 and mx < 3e-6, (K, mean, mx)
