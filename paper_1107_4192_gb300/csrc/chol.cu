@@ -20,20 +20,52 @@ template <> int potrf_block<float>() { return 128; }
 // Factors the n x n (n <= NB) lower triangle at A in shared memory, writes L
 // back (lower triangle only) and L^{-1} to dinv (leading dimension ldd, zero
 // above the diagonal).  The block is padded to NB with an identity, so the
-// algorithm always runs on NB = 32 * P rows:
-//   for each 32-wide panel: one warp factors the 32 x 32 diagonal block in
-//   registers (shuffles, no block barrier) and inverts it; the rows below are
-//   solved against that inverse; the trailing lower triangle gets a rank-32
-//   update with register-blocked threads.
-// The inverse is then assembled by block forward substitution,
-//   X_pq = -X_pp sum_{r=q}^{p-1} L_pr X_rq.
+// algorithm always runs on NB = 32 * NP rows:
+//   for each 32-wide panel, the tall panel (its diagonal block and all rows
+//   below) is factored column by column, each warp holding 32 rows in
+//   registers; one warp owns the diagonal block and publishes the pivot and
+//   the column through shared memory, a named barrier per column;
+//   the trailing lower triangle then gets a rank-32 update.
+// The inverse follows once L is complete: each 32 x 32 diagonal block is
+// inverted by one warp (lane c solves for column c), and the off-diagonal
+// blocks are filled by recursive doubling on 32- then 64-wide halves,
+//   X_BA = -X_BB (L_BA X_AA).
 template <typename T, int NB>
 struct DiagSmem {
-  static constexpr int LD = NB + 1;
+  static constexpr int LD = NB + 1;     // odd stride: rows and columns both free of bank conflicts
   static constexpr int NP = NB / 32;
-  static constexpr int TSZ = NP * 32 * 33;
-  static constexpr size_t bytes = (2ull * NB * LD + TSZ) * sizeof(T);
+  static constexpr int LA = 36;         // 16-byte aligned row stride of the diagonal-block copies
+  static constexpr int al(int x) { return (x + 3) / 4 * 4; }
+  static constexpr int TSZ = NB >= 64 ? (NB / 2) * (NB / 2 + 1) : 4;
+  static constexpr int oS = 0;
+  static constexpr int oX = oS + al(NB * LD);
+  static constexpr int oT = oX + al(NB * LD);
+  static constexpr int oL = oT + al(TSZ);
+  static constexpr int oB = oL + NP * 32 * LA;
+  static constexpr int oR = oB + 2 * LA;
+  static constexpr int total = oR + al(NB);
+  static constexpr size_t bytes = (size_t)total * sizeof(T);
 };
+
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; };
+template <> struct Vec16<double> { using type = double2; };
+
+__device__ __forceinline__ void bar_named(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// q ~ 1 / sqrt(d) and l = sqrt(d) for a pivot d
+__device__ __forceinline__ void pivot(float d, float& q, float& l) {
+  float r = rsqrtf(d);  // one Newton step brings the estimate to about 1 ulp
+  r = r * (1.5f - 0.5f * d * r * r);
+  q = r;
+  l = d * r;
+}
+__device__ __forceinline__ void pivot(double d, double& q, double& l) {
+  l = sqrt(d);
+  q = 1.0 / l;
+}
 
 template <typename T, int BS>
 __device__ __forceinline__ void trailing_update(T* S, int LD, int j0, int r0, int tx, int ty) {
@@ -64,15 +96,64 @@ __device__ __forceinline__ void trailing_update(T* S, int LD, int j0, int r0, in
       if (k0 + b <= i0 + a) S[(i0 + a) * LD + k0 + b] -= acc[a][b];
 }
 
+// One level of the recursive-doubling inverse: for every pair of bs-wide
+// diagonal blocks (A above B), stage 0 forms Tm = L_BA X_AA and stage 1 forms
+// X_BA = -X_BB Tm.  Thread tiles are 4 x 4 with rows and columns strided by
+// bs / 4, so the lanes of a warp read consecutive columns.
+template <typename T, int NB, int bs>
+__device__ __forceinline__ void inverse_level(const T* S, T* X, T* Tm, int tid) {
+  constexpr int LD = NB + 1, R = bs / 4, NPAIR = NB / (2 * bs), LT = bs + 1;
+#pragma unroll
+  for (int stage = 0; stage < 2; ++stage) {
+    for (int t = tid; t < NPAIR * R * R; t += 256) {
+      const int q = t / (R * R), ti = (t % (R * R)) / R, tj = t % R;
+      const int a0 = 2 * q * bs, b0 = a0 + bs;
+      const T* Am = stage == 0 ? S + b0 * LD + a0 : X + b0 * LD + b0;
+      const T* Bm = stage == 0 ? X + a0 * LD + a0 : Tm + q * bs * LT;
+      const int ldb = stage == 0 ? LD : LT;
+      T acc[4][4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+#pragma unroll 4
+      for (int k = 0; k < bs; ++k) {
+        T av[4], bv[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) av[a] = Am[(ti + R * a) * LD + k];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) bv[b] = Bm[k * ldb + tj + R * b];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+      }
+      T* out = stage == 0 ? Tm + q * bs * LT : X + b0 * LD + a0;
+      const int ldo = stage == 0 ? LT : LD;
+      const T sgn = stage == 0 ? T(1) : T(-1);
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) out[(ti + R * a) * ldo + tj + R * b] = sgn * acc[a][b];
+    }
+    __syncthreads();
+  }
+}
+
 template <typename T, int NB>
 __global__ void __launch_bounds__(256, 1) potrf_diag_kernel(T* A, int64_t lda, int n, T* dinv, int64_t ldd,
                                                          int* status, int step, int base) {
   using Cfg = DiagSmem<T, NB>;
-  constexpr int LD = Cfg::LD;
+  using V = typename Vec16<T>::type;
+  constexpr int LD = Cfg::LD, LA = Cfg::LA, E = 16 / sizeof(T);
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* S = reinterpret_cast<T*>(smem_raw);
-  T* X = S + NB * LD;
-  T* Tb = X + NB * LD;
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  T* S = sm + Cfg::oS;
+  T* X = sm + Cfg::oX;
+  T* Tm = sm + Cfg::oT;
+  T* Lal = sm + Cfg::oL;
+  T* buf = sm + Cfg::oB;
+  T* rdiag = sm + Cfg::oR;
   __shared__ int fail;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int warp = tid / 32, lane = tid % 32;
@@ -80,109 +161,108 @@ __global__ void __launch_bounds__(256, 1) potrf_diag_kernel(T* A, int64_t lda, i
   __syncthreads();
   if (fail) return;
 
-  for (int i = tid / 32; i < NB; i += nt / 32) {
-    for (int j = tid % 32; j < NB; j += 32) {
-      T v = T(0);
-      if (i < n && j < n) {
-        if (j <= i) v = A[(int64_t)i * lda + j];
-      } else if (i == j) {
-        v = T(1);
-      }
-      S[i * LD + j] = v;
-      X[i * LD + j] = T(0);
+  // Full, 16-byte aligned blocks move as 16-byte vectors: lane (r, c8) of a
+  // warp takes row 4u + r, vector 8v + c8 of its unit, so both the global
+  // accesses (four 128-byte rows) and the odd-stride shared stores are
+  // conflict-free.  Ragged or unaligned blocks take the scalar path.
+  constexpr int VPR = NB / E, UNITS = NB * VPR / 32, CH = VPR / 8;
+  const bool vec = n == NB && (reinterpret_cast<uintptr_t>(A) & 15) == 0 && lda % E == 0 &&
+                   (reinterpret_cast<uintptr_t>(dinv) & 15) == 0 && ldd % E == 0;
+  if (vec) {
+    V v[UNITS / 8];
+#pragma unroll
+    for (int it = 0; it < UNITS / 8; ++it) {
+      const int u = it * 8 + warp, i = (u / CH) * 4 + lane / 8, j = ((u % CH) * 8 + lane % 8) * E;
+      v[it] = *reinterpret_cast<const V*>(A + (int64_t)i * lda + j);
     }
+#pragma unroll
+    for (int it = 0; it < UNITS / 8; ++it) {
+      const int u = it * 8 + warp, i = (u / CH) * 4 + lane / 8, j = ((u % CH) * 8 + lane % 8) * E;
+      const T* ve = reinterpret_cast<const T*>(&v[it]);
+#pragma unroll
+      for (int e = 0; e < E; ++e) S[i * LD + j + e] = ve[e];  // the upper triangle of S is never read
+    }
+  } else {
+    for (int i = tid / 32; i < NB; i += nt / 32) {
+      for (int j = tid % 32; j < NB; j += 32) {
+        T v = T(0);
+        if (i < n && j < n) {
+          if (j <= i) v = A[(int64_t)i * lda + j];
+        } else if (i == j) {
+          v = T(1);
+        }
+        S[i * LD + j] = v;
+      }
+    }
+  }
+  // the only parts of X read before they are written: the 32 x 32 blocks
+  // above the diagonal inside each 64-wide diagonal block
+  for (int t = tid; t < (NB / 64) * 1024; t += nt) {
+    const int a0 = (t / 1024) * 64, i = (t % 1024) / 32, j = t % 32;
+    X[(a0 + i) * LD + a0 + 32 + j] = T(0);
   }
   __syncthreads();
 
   for (int p = 0; p < Cfg::NP; ++p) {
-    const int j0 = p * 32;
-    // (a) one warp: factor and invert the 32 x 32 diagonal block
-    if (warp == 0) {
-      // Right-looking factorisation of the 32 x 32 block in shared memory, lane i
-      // owning row i.  The step loop stays rolled (small code); inside a step
-      // the 32 column entries come in registers (shuffles) and the row update
-      // is 32 independent predicated load-fma-store triples.
-      T* P = S + j0 * LD + j0;
-      T* Xp = X + j0 * LD + j0;
-      int bad = -1;
-      for (int j = 0; j < 32; ++j) {
-        const T d = P[j * LD + j];
-        if (!(d > T(0) && d < T(INFINITY))) {
-          bad = j;
-          break;
-        }
-        T ljj, rinv;
-        if constexpr (sizeof(T) == 4) {  // reciprocal square root plus one Newton step (about 1 ulp)
-          float r = rsqrtf((float)d);
-          r = r * (1.5f - 0.5f * (float)d * r * r);
-          rinv = (T)r;
-          ljj = d * rinv;
-        } else {
-          ljj = Num<T>::sqrt_(d);
-          rinv = T(1) / ljj;
-        }
-        T lij = T(0);
-        if (lane > j) lij = P[lane * LD + j] * rinv;
-        else if (lane == j) lij = ljj;
-        if (lane >= j) P[lane * LD + j] = lij;
-        Tb[lane] = lij;  // column j, broadcast through shared memory
-        __syncwarp();
-        T col[32];
+    const int j0 = 32 * p;
+    const int nw = Cfg::NP - p;  // warps holding the tall panel, warp 0 on its diagonal block
+    if (warp < nw) {
+      const int i = j0 + 32 * warp + lane;
+      T r[32];
 #pragma unroll
-        for (int k = 0; k < 32; ++k) col[k] = Tb[k];
-        // branch-free: every lane touches all 32 entries of its row, with the
-        // update masked to j < k <= lane (entries above the diagonal stay zero)
+      for (int k = 0; k < 32; ++k) r[k] = S[i * LD + j0 + k];
+      int bad = -1;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        T* bj = buf + (j & 1) * LA;  // two buffers: a column is written while the previous one may be read
+        T q, l;
+        if (warp == 0) {
+          const T d = __shfl_sync(0xffffffffu, r[j], j);
+          if (bad < 0 && !(d > T(0) && d < T(INFINITY))) bad = j;
+          T ljj;
+          pivot(d, q, ljj);
+          l = lane > j ? r[j] * q : (lane == j ? ljj : T(0));
+          bj[lane] = l;
+          if (lane == 0) {
+            bj[32] = q;
+            rdiag[j0 + j] = q;
+          }
+        }
+        bar_named(1, 32 * nw);
+        if (warp != 0) {
+          q = bj[32];
+          l = r[j] * q;
+        }
+        r[j] = l;
+#pragma unroll
+        for (int g = (j + 1) / E; g < 32 / E; ++g) {
+          const V v = reinterpret_cast<const V*>(bj)[g];
+          const T* ve = reinterpret_cast<const T*>(&v);
+#pragma unroll
+          for (int e = 0; e < E; ++e)
+            if (g * E + e > j) r[g * E + e] = fma(-l, ve[e], r[g * E + e]);
+        }
+      }
+      if (warp == 0) {
 #pragma unroll
         for (int k = 0; k < 32; ++k) {
-          const T w = (k > j && k <= lane) ? lij : T(0);
-          P[lane * LD + k] = fma(-w, col[k], P[lane * LD + k]);
+          if (k <= lane) S[i * LD + j0 + k] = r[k];
+          Lal[(p * 32 + lane) * LA + k] = k <= lane ? r[k] : T(0);
         }
-        __syncwarp();  // the next pivot is read from another lane's row
-      }
-      __syncwarp();
-      if (bad >= 0) {
-        if (lane == 0) {
+        if (lane == 0 && bad >= 0) {
           fail = 1;
           status_set(status, KF_ERR_NOT_PD, step, base + j0 + bad);
         }
       } else {
-        // lane c computes column c of the block inverse, rows in order:
-        // x_i = (delta_ic - sum_{c<=k<i} L_ik x_k) / L_ii
-        for (int i = 0; i < 32; ++i) {
-          // branch-free: X is zero above its diagonal (k < lane), and k >= i is masked
-          T acc0 = (i == lane) ? T(1) : T(0), acc1 = T(0);
 #pragma unroll
-          for (int k = 0; k < 32; k += 2) {
-            const T l0 = k < i ? P[i * LD + k] : T(0);
-            const T l1 = k + 1 < i ? P[i * LD + k + 1] : T(0);
-            acc0 = fma(-l0, Xp[k * LD + lane], acc0);
-            acc1 = fma(-l1, Xp[(k + 1) * LD + lane], acc1);
-          }
-          Xp[i * LD + lane] = i >= lane ? (acc0 + acc1) / P[i * LD + i] : T(0);
-        }
+        for (int k = 0; k < 32; ++k) S[i * LD + j0 + k] = r[k];
       }
     }
     __syncthreads();
     if (fail) return;
     const int r0 = j0 + 32, R = NB - r0;
     if (R <= 0) break;
-    // (b) panel below: L[i][j0+c] = sum_{k<=c} A[i][j0+k] X[j0+c][j0+k], staged through Tb
-    for (int item = tid; item < R * 8; item += nt) {
-      const int i = r0 + item / 8, c0 = (item % 8) * 4;
-      T o[4] = {T(0), T(0), T(0), T(0)};
-#pragma unroll 8
-      for (int k = 0; k < 32; ++k) {
-        const T av = S[i * LD + j0 + k];
-#pragma unroll
-        for (int cc = 0; cc < 4; ++cc) o[cc] = fma(av, X[(j0 + c0 + cc) * LD + j0 + k], o[cc]);
-      }
-#pragma unroll
-      for (int cc = 0; cc < 4; ++cc) Tb[(item / 8) * 33 + c0 + cc] = o[cc];
-    }
-    __syncthreads();
-    for (int idx = tid; idx < R * 32; idx += nt) S[(r0 + idx / 32) * LD + j0 + idx % 32] = Tb[(idx / 32) * 33 + idx % 32];
-    __syncthreads();
-    // (c) trailing rank-32 update of the lower triangle, 16 x 16 threads
+    // trailing rank-32 update of the lower triangle, 16 x 16 threads
     {
       const int tx = tid % 16, ty = tid / 16;
       if (R == 96) trailing_update<T, 6>(S, LD, j0, r0, tx, ty);
@@ -192,43 +272,57 @@ __global__ void __launch_bounds__(256, 1) potrf_diag_kernel(T* A, int64_t lda, i
     __syncthreads();
   }
 
-  // (d) assemble the inverse: X_pq = -X_pp sum_{r=q}^{p-1} L_pr X_rq
-  for (int p = 1; p < Cfg::NP; ++p) {
-    for (int item = tid; item < p * 32 * 8; item += nt) {
-      const int q = item / 256, rr = (item % 256) / 8, c0 = (item % 8) * 4;
-      T o[4] = {T(0), T(0), T(0), T(0)};
-      for (int kb = 32 * q; kb < 32 * p; kb += 32) {
-#pragma unroll 8
-        for (int kk = 0; kk < 32; ++kk) {
-          const int k = kb + kk;
-          const T lv = S[(32 * p + rr) * LD + k];
+  // diagonal-block inverses: warp p, lane c: x_i = (delta_ic - sum_{k<i} L_ik x_k) / L_ii
+  if (warp < Cfg::NP) {
+    const T* Lp = Lal + warp * 32 * LA;
+    T x[32];
 #pragma unroll
-          for (int cc = 0; cc < 4; ++cc) o[cc] = fma(lv, X[k * LD + 32 * q + c0 + cc], o[cc]);
-        }
+    for (int i = 0; i < 32; ++i) {
+      T s = i == lane ? T(1) : T(0);
+#pragma unroll
+      for (int g = 0; g < (i + E - 1) / E; ++g) {
+        const V v = reinterpret_cast<const V*>(Lp + i * LA)[g];
+        const T* ve = reinterpret_cast<const T*>(&v);
+#pragma unroll
+        for (int e = 0; e < E; ++e)
+          if (g * E + e < i) s = fma(-ve[e], x[g * E + e], s);
       }
-#pragma unroll
-      for (int cc = 0; cc < 4; ++cc) Tb[(q * 32 + rr) * 33 + c0 + cc] = o[cc];
+      x[i] = s * rdiag[32 * warp + i];
     }
-    __syncthreads();
-    for (int item = tid; item < p * 32 * 8; item += nt) {
-      const int q = item / 256, rr = (item % 256) / 8, c0 = (item % 8) * 4;
-      T o[4] = {T(0), T(0), T(0), T(0)};
-#pragma unroll 8
-      for (int k = 0; k < 32; ++k) {  // X_pp is zero above its diagonal
-        const T xv = X[(32 * p + rr) * LD + 32 * p + k];
 #pragma unroll
-        for (int cc = 0; cc < 4; ++cc) o[cc] = fma(xv, Tb[(q * 32 + k) * 33 + c0 + cc], o[cc]);
-      }
-#pragma unroll
-      for (int cc = 0; cc < 4; ++cc) X[(32 * p + rr) * LD + 32 * q + c0 + cc] = -o[cc];
-    }
-    __syncthreads();
+    for (int i = 0; i < 32; ++i) X[(32 * warp + i) * LD + 32 * warp + lane] = x[i];
   }
+  __syncthreads();
+  if constexpr (NB >= 64) inverse_level<T, NB, 32>(S, X, Tm, tid);
+  if constexpr (NB >= 128) inverse_level<T, NB, 64>(S, X, Tm, tid);
 
-  for (int i = tid / 32; i < n; i += nt / 32) {
-    for (int j = tid % 32; j < n; j += 32) {
-      if (j <= i) A[(int64_t)i * lda + j] = S[i * LD + j];
-      dinv[(int64_t)i * ldd + j] = j <= i ? X[i * LD + j] : T(0);
+  if (vec) {
+#pragma unroll 4
+    for (int it = 0; it < UNITS / 8; ++it) {
+      const int u = it * 8 + warp, i = (u / CH) * 4 + lane / 8, j = ((u % CH) * 8 + lane % 8) * E;
+      V lv, xv;
+      T* le = reinterpret_cast<T*>(&lv);
+      T* xe = reinterpret_cast<T*>(&xv);
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        le[e] = S[i * LD + j + e];
+        xe[e] = j + e <= i ? X[i * LD + j + e] : T(0);
+      }
+      *reinterpret_cast<V*>(dinv + (int64_t)i * ldd + j) = xv;
+      if (j + E - 1 <= i) {
+        *reinterpret_cast<V*>(A + (int64_t)i * lda + j) = lv;
+      } else {
+#pragma unroll
+        for (int e = 0; e < E; ++e)
+          if (j + e <= i) A[(int64_t)i * lda + j + e] = le[e];
+      }
+    }
+  } else {
+    for (int i = tid / 32; i < n; i += nt / 32) {
+      for (int j = tid % 32; j < n; j += 32) {
+        if (j <= i) A[(int64_t)i * lda + j] = S[i * LD + j];
+        dinv[(int64_t)i * ldd + j] = j <= i ? X[i * LD + j] : T(0);
+      }
     }
   }
 }
