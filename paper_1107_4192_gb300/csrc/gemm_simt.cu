@@ -123,6 +123,10 @@ kf_status gemm_simt(cudaStream_t s, bool transB, const GemmParams<T>& p) {
   using C = SimtCfg<T>;
   if (p.M <= 0 || p.N <= 0) return KF_OK;
   if (p.K < 0) return KF_ERR_ARG;
+  if constexpr (sizeof(T) == 4) {
+    // aligned float32 operands take the pipelined kernel (same products, same order)
+    if (gemm_small_ok(transB, p)) return gemm_small(s, transB, p);
+  }
   dim3 grid;
   if (p.sym) {
     if (p.M != p.N) return KF_ERR_ARG;

@@ -56,6 +56,10 @@ struct GemmParams {
 // (C = A B^T) else K x N row-major (C = A B).  Plain CUDA-core FMA tiles.
 template <typename T>
 kf_status gemm_simt(cudaStream_t s, bool transB, const GemmParams<T>& p);
+// Pipelined float32 product for small operands (gemm_small.cu); needs 16-byte
+// aligned A and B, lda, ldb and K multiples of 4 (and N when !transB).
+bool gemm_small_ok(bool transB, const GemmParams<float>& p);
+kf_status gemm_small(cudaStream_t s, bool transB, const GemmParams<float>& p);
 
 // Blocked right-looking Cholesky A = L L^T of the n x n lower triangle (in
 // place; the strict upper triangle is left untouched).  dinv receives the

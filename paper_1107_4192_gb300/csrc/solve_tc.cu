@@ -9,7 +9,9 @@
 //    A22 <- A22 - L21 L21^T;  L22 = chol(A22);
 //  - triangular inverse on the same halves: W21 = -W22 (L21 W11);
 //  - the diagonal blocks (nb = 128) are factored and inverted by one CTA each.
-// Products with a triangular operand skip the k-tiles outside its band.
+// Products with a triangular operand skip the k-tiles outside its band.  The
+// small products near the leaves run in float32 on the CUDA cores, where
+// their latency is a fraction of a tensor-core launch.
 // This replaces the two triangular solves with N right-hand sides by a
 // triangular inverse and two triangular products (2.67 N^3 instead of
 // 2.33 N^3 flops), in exchange for large, fully parallel products only.
@@ -42,7 +44,15 @@ struct Ctx {
 
 int split_point(int n, int nb) { return (int)round_up((n + 1) / 2, nb); }
 
-kf_status gemm(Ctx& c, const GemmParams<float>& g, bool transB) { return tc_gemm_split(c.s, *c.sc, g, 3, transB); }
+// Products up to about 640^3 are latency-bound on the tensor-core path (an
+// operand split plus the tensor-core kernel cost ~30 us at any size below
+// 512^3); they run as pipelined float32 CUDA-core products instead.
+constexpr int64_t kSmallWork = int64_t(1) << 28;
+
+kf_status gemm(Ctx& c, const GemmParams<float>& g, bool transB) {
+  if ((int64_t)g.M * g.N * g.K <= kSmallWork && gemm_small_ok(transB, g)) return gemm_small(c.s, transB, g);
+  return tc_gemm_split(c.s, *c.sc, g, 3, transB);
+}
 
 kf_status trtri_rec(Ctx& c, int off, int n) {
   if (c.done.count({off, n})) return KF_OK;

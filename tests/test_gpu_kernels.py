@@ -28,7 +28,8 @@ def _dev(a, dt):
 
 @pytest.mark.parametrize("dtype", [0, 1])
 @pytest.mark.parametrize("transB", [0, 1])
-@pytest.mark.parametrize("M,N,K", [(1, 1, 1), (7, 5, 3), (129, 65, 200), (300, 130, 77), (64, 64, 0)])
+@pytest.mark.parametrize("M,N,K", [(1, 1, 1), (7, 5, 3), (129, 65, 200), (300, 130, 77), (64, 64, 0),
+                                   (256, 260, 128), (520, 132, 1028)])
 def test_gemm(dtype, transB, M, N, K):
     rng = np.random.default_rng(M * 1000 + N * 10 + K)
     A = rng.standard_normal((M, K))
