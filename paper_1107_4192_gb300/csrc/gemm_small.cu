@@ -17,7 +17,7 @@ namespace kfm {
 
 namespace {
 
-constexpr int kBK = 16, kStages = 4, kThreads = 256;
+constexpr int kBK = 16, kThreads = 256;
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool pred) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -35,7 +35,7 @@ __device__ __forceinline__ void cp_async_wait() {
 // N x K (TB), else [k][n] (row stride BN + 4).  Thread (ty, tx) owns rows
 // ty + 16 i and columns tx + 16 j (TB) or 4 tx + j (not TB), which keeps every
 // shared-memory read free of bank conflicts.
-template <int BM, int BN, bool TB>
+template <int BM, int BN, int kStages, bool TB>
 __global__ void __launch_bounds__(kThreads) gemm_small_kernel(GemmParams<float> p) {
   constexpr int TM = BM / 16, TN = BN / 16;
   constexpr int LDA = kBK + 4;
@@ -128,14 +128,25 @@ __global__ void __launch_bounds__(kThreads) gemm_small_kernel(GemmParams<float> 
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           float bv[TN];
-          if constexpr (TN == 4) {
+          if constexpr (TN == 8) {
+            const float4 b4 = *reinterpret_cast<const float4*>(b_s + (4 * kq + e) * LDB + TN * tx);
+            const float4 b5 = *reinterpret_cast<const float4*>(b_s + (4 * kq + e) * LDB + TN * tx + 4);
+            bv[0] = b4.x;
+            bv[1] = b4.y;
+            bv[2] = b4.z;
+            bv[3] = b4.w;
+            bv[4] = b5.x;
+            bv[5] = b5.y;
+            bv[6] = b5.z;
+            bv[7] = b5.w;
+          } else if constexpr (TN == 4) {
             const float4 b4 = *reinterpret_cast<const float4*>(b_s + (4 * kq + e) * LDB + TN * tx);
             bv[0] = b4.x;
             bv[1] = b4.y;
             bv[2] = b4.z;
             bv[3] = b4.w;
           } else {
-            static_assert(TN == 2, "32- or 64-wide tiles");
+            static_assert(TN == 2, "32-, 64- or 128-wide tiles");
             const float2 b2 = *reinterpret_cast<const float2*>(b_s + (4 * kq + e) * LDB + TN * tx);
             bv[0] = b2.x;
             bv[1] = b2.y;
@@ -168,34 +179,69 @@ __global__ void __launch_bounds__(kThreads) gemm_small_kernel(GemmParams<float> 
   }
 }
 
-template <int BM, int BN>
+template <int BM, int BN, int STAGES>
 kf_status launch_small(cudaStream_t s, bool transB, const GemmParams<float>& p) {
   const dim3 grid((unsigned)ceil_div(p.N, BN), (unsigned)ceil_div(p.M, BM));
   if (grid.y > 65535) return KF_ERR_ARG;
   if (transB)
-    gemm_small_kernel<BM, BN, true><<<grid, kThreads, 0, s>>>(p);
+    gemm_small_kernel<BM, BN, STAGES, true><<<grid, kThreads, 0, s>>>(p);
   else
-    gemm_small_kernel<BM, BN, false><<<grid, kThreads, 0, s>>>(p);
+    gemm_small_kernel<BM, BN, STAGES, false><<<grid, kThreads, 0, s>>>(p);
   note_launch();
   return launch_check("gemm_small");
 }
 
 bool aligned16(const void* ptr) { return (reinterpret_cast<uintptr_t>(ptr) & 15) == 0; }
 
+// Whether the ra x ca block at a and the rb x cb block at b (row strides la,
+// lb) share an element.  Exact when la == lb and b's columns do not wrap past
+// the stride; conservative (true) otherwise.
+bool blocks_overlap(const float* a, int64_t la, int64_t ra, int64_t ca, const float* b, int64_t lb, int64_t rb,
+                    int64_t cb) {
+  if (ra <= 0 || ca <= 0 || rb <= 0 || cb <= 0) return false;
+  const float* a_end = a + (ra - 1) * la + ca;
+  const float* b_end = b + (rb - 1) * lb + cb;
+  if (a_end <= b || b_end <= a) return false;
+  if (la != lb || la <= 0) return true;
+  const int64_t d = b - a;
+  const int64_t dr = d >= 0 ? d / la : -((-d + la - 1) / la);
+  const int64_t dc = d - dr * la;  // 0 <= dc < la
+  if (dc + cb > la) return true;
+  const bool rows = dr < ra && dr + rb > 0;
+  const bool cols = dc < ca && dc + cb > 0;
+  return rows && cols;
+}
+
 }  // namespace
+
+SmallAlias gemm_small_alias(bool transB, const GemmParams<float>& p) {
+  if (!p.out) return SmallAlias::kNone;
+  const int64_t rb = transB ? p.N : p.K, cb = transB ? p.K : p.N;
+  if (blocks_overlap(p.out, p.ldo, p.M, p.N, p.B, p.ldb, rb, cb)) return SmallAlias::kOther;
+  if (blocks_overlap(p.out, p.ldo, p.M, p.N, p.A, p.lda, p.M, p.K)) {
+    // out and A may be the same rows (an in-place row transform): safe when one
+    // CTA owns whole rows of out and reads each A row only from those rows
+    return p.A == p.out && p.lda == p.ldo && p.N <= 128 ? SmallAlias::kSameRows : SmallAlias::kOther;
+  }
+  return SmallAlias::kNone;
+}
 
 bool gemm_small_ok(bool transB, const GemmParams<float>& p) {
   if (p.transA || p.M <= 0 || p.N <= 0 || p.K <= 0) return false;
   if (p.K % 4 || !aligned16(p.A) || p.lda % 4 || !aligned16(p.B) || p.ldb % 4) return false;
   if (!transB && p.N % 4) return false;
   if (p.sym && p.M != p.N) return false;
-  return true;
+  return gemm_small_alias(transB, p) != SmallAlias::kOther;
 }
 
 kf_status gemm_small(cudaStream_t s, bool transB, const GemmParams<float>& p) {
   if (!gemm_small_ok(transB, p)) return KF_ERR_ARG;
-  if ((int64_t)p.M * p.N <= 256 * 256) return launch_small<32, 32>(s, transB, p);
-  return launch_small<64, 64>(s, transB, p);
+  // In place (out == A): every CTA must own all N <= 128 columns of its rows, so
+  // that no other CTA writes a row it still reads; the CTA reads its rows
+  // completely before its epilogue writes them.
+  if (gemm_small_alias(transB, p) == SmallAlias::kSameRows) return launch_small<32, 128, 3>(s, transB, p);
+  if ((int64_t)p.M * p.N <= 256 * 256) return launch_small<32, 32, 4>(s, transB, p);
+  return launch_small<64, 64, 4>(s, transB, p);
 }
 
 }  // namespace kfm

@@ -57,7 +57,11 @@ struct GemmParams {
 template <typename T>
 kf_status gemm_simt(cudaStream_t s, bool transB, const GemmParams<T>& p);
 // Pipelined float32 product for small operands (gemm_small.cu); needs 16-byte
-// aligned A and B, lda, ldb and K multiples of 4 (and N when !transB).
+// aligned A and B, lda, ldb and K multiples of 4 (and N when !transB), and out
+// must not overlap an operand, except out == A with N <= 128 (an in-place row
+// transform, run with tiles that own whole rows).
+enum class SmallAlias { kNone, kSameRows, kOther };
+SmallAlias gemm_small_alias(bool transB, const GemmParams<float>& p);
 bool gemm_small_ok(bool transB, const GemmParams<float>& p);
 kf_status gemm_small(cudaStream_t s, bool transB, const GemmParams<float>& p);
 

@@ -50,7 +50,20 @@ int split_point(int n, int nb) { return (int)round_up((n + 1) / 2, nb); }
 constexpr int64_t kSmallWork = int64_t(1) << 28;
 
 kf_status gemm(Ctx& c, const GemmParams<float>& g, bool transB) {
-  if ((int64_t)g.M * g.N * g.K <= kSmallWork && gemm_small_ok(transB, g)) return gemm_small(c.s, transB, g);
+  if ((int64_t)g.M * g.N * g.K <= kSmallWork) {
+    if (gemm_small_ok(transB, g)) return gemm_small(c.s, transB, g);
+    if (gemm_small_alias(transB, g) == SmallAlias::kOther && g.A != c.T && g.B != c.T && !g.cin && !g.csub) {
+      // in place wider than one tile (L21 = A21 W11^T): through the scratch T
+      GemmParams<float> t = g;
+      t.out = c.T;
+      t.ldo = c.ldt;
+      if (gemm_small_ok(transB, t)) {
+        KF_TRY(gemm_small(c.s, transB, t));
+        return copy2d<float, float>(c.s, g.out, g.ldo, c.T, c.ldt, g.M, g.N);
+      }
+    }
+  }
+  // the tensor-core path splits both operands into scratch first, so in place is safe there
   return tc_gemm_split(c.s, *c.sc, g, 3, transB);
 }
 

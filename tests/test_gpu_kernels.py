@@ -44,6 +44,21 @@ def test_gemm(dtype, transB, M, N, K):
     assert np.linalg.norm(got - ref) <= tol * max(np.linalg.norm(ref), 1e-300) * max(1, np.sqrt(K) / 4)
 
 
+@pytest.mark.parametrize("transB", [0, 1])
+@pytest.mark.parametrize("M,N", [(1000, 128), (77, 64), (3000, 96)])
+def test_gemm_in_place_rows(transB, M, N):
+    """C = C B (or C B^T) with the output overwriting A: the row transform that
+    the blocked solves apply in place (N <= 128)."""
+    rng = np.random.default_rng(M + N + transB)
+    A = rng.standard_normal((M, N))
+    Bm = rng.standard_normal((N, N))
+    ref = A @ (Bm.T if transB else Bm)
+    dA, dB = _dev(A, 1), _dev(Bm, 1)
+    B.kfx_gemm(1, transB, 0, M, N, N, 1.0, dA, N, dB, N, 0.0, dA, N)
+    got = dA.double().cpu().numpy()
+    assert np.linalg.norm(got - ref) <= 2e-5 * np.linalg.norm(ref) * max(1, np.sqrt(N) / 4)
+
+
 @pytest.mark.parametrize("dtype", [0, 1])
 @pytest.mark.parametrize("n,K", [(1, 3), (63, 64), (130, 20), (257, 129)])
 def test_gemm_symmetric_mirror(dtype, n, K):

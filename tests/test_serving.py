@@ -79,3 +79,24 @@ def test_recompute_mode_under_a_small_budget(built):
             assert np.array_equal(a.outputs[k], b.outputs[k]), k
     s = serve.summarize(tight)
     assert s["completed"] == 2 and s["recompute_requests"] >= 1
+
+
+@pytest.mark.gpu
+def test_mid_size_concurrent_equals_alone(built):
+    """Six 1024..1536-wide epochs at once: wide enough that the solve runs its
+    small products and leaves on the CUDA cores while other plans' kernels
+    share the GPU, so a product whose CTAs read what a sibling CTA writes
+    would show up here as a difference (or a failed factorisation)."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    probs = [synth.mesh_problem(N, m, 10, seed=50 + i, identity_F=(i % 2 == 0))
+             for i, (N, m) in enumerate([(1024, 64), (1152, 128), (1280, 64), (1408, 128), (1536, 64), (1024, 128)])]
+    reqs = lambda: [serve.Request(i, 0.0, p, prec=B.KF_PREC_MIXED_BF16X3, solve_prec=B.KF_SOLVE_FP32)
+                    for i, p in enumerate(probs)]
+    alone = serve.Server(max_slots=1, keep_outputs=True).run(reqs())
+    mix = serve.Server(max_slots=6, keep_outputs=True).run(reqs())
+    for a, b in zip(alone, mix):
+        assert a.status == b.status == "ok", (a.status, b.status)
+        for k in a.outputs:
+            assert np.array_equal(a.outputs[k], b.outputs[k]), (a.rid, k)
