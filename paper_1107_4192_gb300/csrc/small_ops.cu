@@ -283,66 +283,134 @@ kf_status split_bf16_t(cudaStream_t s, int64_t rows, int64_t cols, const float* 
   return launch_check("split_bf16_t");
 }
 
-// One 32 x 32 output tile of the planes per CTA; blockIdx.z picks the operand.
-// The first slice of a float64 source is taken in float64 (so the next slices
-// keep bits below float32's), the rest in float32 arithmetic, which is exact
-// for these residuals.
+__device__ __forceinline__ int64_t ceil_div_d(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Operand split for the split-bf16 products: plane s of row r holds slice s
+// of op(X)[r][k] for k < ldh (zero for k >= cols).  The first slice of a
+// float64 source is rounded from float64 (so the next slices keep bits below
+// float32's), the rest in float32 arithmetic, which is exact for these
+// residuals.  Stores are 16 bytes (8 values) per plane.
+__device__ __forceinline__ uint4 pack8(const __nv_bfloat16 (&h)[8]) {
+  uint32_t w[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    w[i] = (uint32_t)__bfloat16_as_ushort(h[2 * i]) | ((uint32_t)__bfloat16_as_ushort(h[2 * i + 1]) << 16);
+  return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
 template <typename S>
-__device__ __forceinline__ void split_tile(const SplitOp& op, int n, int64_t ldh, S (*tile)[33]) {
-  const int64_t r0 = (int64_t)blockIdx.x * 32, k0 = (int64_t)blockIdx.y * 32;
-  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;  // 32 x 8 threads
-  const S* src = static_cast<const S*>(op.src);
-  if (op.trans) {
-    for (int i = ty; i < 32; i += 8) {
-      const int64_t k = k0 + i, r = r0 + tx;
-      tile[i][tx] = (k < op.cols && r < op.rows) ? src[k * op.ld + r] : S(0);
-    }
-  } else {
-    for (int i = ty; i < 32; i += 8) {
-      const int64_t r = r0 + i, k = k0 + tx;
-      tile[tx][i] = (k < op.cols && r < op.rows) ? src[r * op.ld + k] : S(0);
+__device__ __forceinline__ void split8(const S (&v)[8], __nv_bfloat16* p0, __nv_bfloat16* p1, __nv_bfloat16* p2,
+                                       int n, int64_t off) {
+  float rest[8];
+  __nv_bfloat16 h[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    if constexpr (sizeof(S) == 8) {
+      h[e] = __double2bfloat16(v[e]);
+      rest[e] = (float)(v[e] - (double)__bfloat162float(h[e]));
+    } else {
+      h[e] = __float2bfloat16_rn(v[e]);
+      rest[e] = v[e] - __bfloat162float(h[e]);
     }
   }
-  __syncthreads();
-  for (int i = ty; i < 32; i += 8) {
-    const int64_t r = r0 + i, k = k0 + tx;
-    if (r >= op.rows || k >= ldh) continue;
-    const S v0 = tile[tx][i];
-    float v;
-    if (sizeof(S) == 8) {
-      const __nv_bfloat16 h = __double2bfloat16((double)v0);
-      op.planes[0][r * ldh + k] = h;
-      v = (float)((double)v0 - (double)__bfloat162float(h));
-    } else {
-      const __nv_bfloat16 h = __float2bfloat16_rn((float)v0);
-      op.planes[0][r * ldh + k] = h;
-      v = (float)v0 - __bfloat162float(h);
+  *reinterpret_cast<uint4*>(p0 + off) = pack8(h);
+  for (int s = 1; s < n; ++s) {
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      h[e] = __float2bfloat16_rn(rest[e]);
+      rest[e] -= __bfloat162float(h[e]);
     }
-    for (int s = 1; s < n; ++s) {
-      const __nv_bfloat16 h = __float2bfloat16_rn(v);
-      op.planes[s][r * ldh + k] = h;
-      v -= __bfloat162float(h);
+    *reinterpret_cast<uint4*>((s == 1 ? p1 : p2) + off) = pack8(h);
+  }
+}
+
+// Untransposed source (op(X) = X, rows x cols, row stride ld): one thread per
+// 8 consecutive values of a row, 16-byte loads where the row allows.
+template <typename S>
+__device__ __forceinline__ void split_rows(const SplitOp& op, int n, int64_t ldh) {
+  const S* src = static_cast<const S*>(op.src);
+  constexpr int VE = 16 / sizeof(S);
+  const bool vec = (reinterpret_cast<uintptr_t>(src) & 15) == 0 && op.ld % VE == 0;
+  const int64_t per_row = ldh / 8, units = op.rows * per_row;
+  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < units; u += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = u / per_row, k = (u % per_row) * 8;
+    const S* row = src + r * op.ld;
+    S v[8];
+    if (vec && k + 8 <= op.cols) {
+#pragma unroll
+      for (int e = 0; e < 8; e += VE) {
+        if constexpr (sizeof(S) == 8) {
+          const double2 d = *reinterpret_cast<const double2*>(row + k + e);
+          v[e] = d.x;
+          v[e + 1] = d.y;
+        } else {
+          const float4 f = *reinterpret_cast<const float4*>(row + k + e);
+          v[e] = f.x;
+          v[e + 1] = f.y;
+          v[e + 2] = f.z;
+          v[e + 3] = f.w;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) v[e] = k + e < op.cols ? row[k + e] : S(0);
+    }
+    split8<S>(v, op.planes[0], op.planes[1], op.planes[2], n, r * ldh + k);
+  }
+}
+
+// Transposed source (stored cols x rows, op(X)[r][k] = X[k][r]): 64 x 64 tiles
+// through shared memory, read along source rows, written 8 values per store.
+template <typename S>
+__device__ __forceinline__ void split_cols(const SplitOp& op, int n, int64_t ldh, S (*tile)[65]) {
+  const S* src = static_cast<const S*>(op.src);
+  const int64_t tr = ceil_div_d(op.rows, 64), tk = ldh / 64, tiles = tr * tk;
+  const int t = threadIdx.x;
+  for (int64_t b = blockIdx.x; b < tiles; b += gridDim.x) {
+    const int64_t r0 = (b % tr) * 64, k0 = (b / tr) * 64;
+    __syncthreads();  // the previous tile's reads are done
+    for (int i = t / 64; i < 64; i += 4) {  // tile[i][c] = X[k0 + i][r0 + c]
+      const int c = t % 64;
+      const int64_t k = k0 + i, r = r0 + c;
+      tile[i][c] = (k < op.cols && r < op.rows) ? src[k * op.ld + r] : S(0);
+    }
+    __syncthreads();
+    for (int w = t; w < 64 * 8; w += 256) {
+      const int c = w / 8, kc = (w % 8) * 8;
+      const int64_t r = r0 + c;
+      if (r >= op.rows) continue;
+      S v[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) v[e] = tile[kc + e][c];
+      split8<S>(v, op.planes[0], op.planes[1], op.planes[2], n, r * ldh + k0 + kc);
     }
   }
 }
 
-__global__ void split_bf16_pair_kernel(SplitOp a, SplitOp b, int n, int64_t ldh) {
-  __shared__ double tile_d[32][33];
-  const SplitOp& op = blockIdx.z == 0 ? a : b;
-  const int64_t r0 = (int64_t)blockIdx.x * 32, k0 = (int64_t)blockIdx.y * 32;
-  if (r0 >= op.rows || k0 >= ldh) return;
-  if (op.f64)
-    split_tile<double>(op, n, ldh, tile_d);
-  else
-    split_tile<float>(op, n, ldh, reinterpret_cast<float(*)[33]>(tile_d));
+__global__ void __launch_bounds__(256) split_bf16_pair_kernel(SplitOp a, SplitOp b, int n, int64_t ldh) {
+  __shared__ double tile_d[64][65];
+  const SplitOp op = blockIdx.y == 0 ? a : b;
+  if (op.rows <= 0) return;
+  if (op.trans) {
+    if (op.f64)
+      split_cols<double>(op, n, ldh, tile_d);
+    else
+      split_cols<float>(op, n, ldh, reinterpret_cast<float(*)[65]>(tile_d));
+  } else {
+    if (op.f64)
+      split_rows<double>(op, n, ldh);
+    else
+      split_rows<float>(op, n, ldh);
+  }
 }
 
 kf_status split_bf16_pair(cudaStream_t s, const SplitOp& a, const SplitOp& b, int n, int64_t ldh) {
-  if (n < 1 || n > 3) return KF_ERR_ARG;
+  if (n < 1 || n > 3 || ldh % 64) return KF_ERR_ARG;
   const int64_t rows = std::max(a.rows, b.rows);
   if (rows <= 0) return KF_OK;
-  if (ceil_div(rows, 32) > 0x7fffffff || ceil_div(ldh, 32) > 65535) return KF_ERR_ARG;
-  dim3 grid((unsigned)ceil_div(rows, 32), (unsigned)ceil_div(ldh, 32), 2);
+  // enough CTAs to fill the GPU for the large operands, fewer for small ones
+  const int64_t work = std::max(ceil_div(a.rows, 64) * (ldh / 64), ceil_div(b.rows, 64) * (ldh / 64));
+  const dim3 grid((unsigned)std::min<int64_t>(std::max<int64_t>(work, 1), 152 * 8), 2);
   split_bf16_pair_kernel<<<grid, 256, 0, s>>>(a, b, n, ldh);
   note_launch();
   return launch_check("split_bf16_pair");
