@@ -20,6 +20,14 @@ __device__ __forceinline__ void epilogue_store(const GemmParams<T>& p, int gi, i
   T v = vpre;
   if (p.csub) v -= p.csub[(int64_t)gi * p.ldcsub + gj];
   const bool mirror = (p.sym == 1) && gi != gj;
+  if (p.gain_q) {
+    const T qi = (T)(p.gain_q_kind == 0 ? p.gain_q[0] : p.gain_q[gi]);
+    const T qj = (T)(p.gain_q_kind == 0 ? p.gain_q[0] : p.gain_q[gj]);
+    const T d = gi == gj ? T(1) : T(0);
+    p.out[(int64_t)gi * p.ldo + gj] = d - qi * vpre;
+    if (mirror) p.out[(int64_t)gj * p.ldo + gi] = d - qj * vpre;
+    return;
+  }
   if (p.out) {
     p.out[(int64_t)gi * p.ldo + gj] = v;
     if (mirror) p.out[(int64_t)gj * p.ldo + gi] = v;

@@ -50,6 +50,11 @@ struct GemmParams {
   // k-tiles outside the band are skipped; 0 = dense.
   int transA = 0;
   int tri_a = 0, tri_b = 0;
+  // Smoother gain from an inverse (J = I - Q P^{-1}, F = I): when gain_q is
+  // set, out receives delta_ij - q_i (alpha acc + beta cin) with q_i = gain_q[0]
+  // (gain_q_kind 0) or gain_q[i] (1); a mirrored element uses q_j.
+  const double* gain_q = nullptr;
+  int gain_q_kind = -1;
 };
 
 // C = op(A) x op(B) with A: M x K row-major; B: N x K row-major when transB

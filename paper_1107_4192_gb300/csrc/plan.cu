@@ -748,8 +748,7 @@ kf_status run_smoother(kf_plan_s* p, double* x_smooth, double* diagP_smooth, dou
       }
       Prof pg(p, KF_KC_SOLVE_GAIN);
       if (tc_solve && p->d.f_kind == KF_F_IDENTITY && p->d.q_kind != KF_COV_DENSE) {
-        KF_TRY(gain_identity_tc(s, p->tc, (int)N, p->Wi, ldN, p->d.q_kind, p->Q, (float*)p->tmpN, ldN, (float*)Jb,
-                                ldN, p->status));
+        KF_TRY(gain_identity_tc(s, p->tc, (int)N, p->Wi, ldN, p->d.q_kind, p->Q, (float*)Jb, ldN, p->status));
       } else if (tc_solve) {
         if (Bm != Pt) {  // Bm lives in tmpN, which the products below use as scratch
           KF_TRY((copy2d<B, B>(s, (B*)Jb, ldN, Bm, ldN, N, N)));

@@ -12,54 +12,153 @@ __device__ __forceinline__ double cov_value(int kind, const double* q, int64_t n
   return 0.0;
 }
 
+// Row-major elementwise kernels move 4 consecutive elements of a row per
+// unit with 16-byte accesses where the rows allow it, and each thread keeps
+// kUnroll units in flight (the covariance copies and updates are N x N sweeps
+// bound by HBM bandwidth).
+constexpr int kUnroll = 4;
+
+template <typename T>
+__device__ __forceinline__ bool aligned_rows(const T* p, int64_t ld) {
+  return (reinterpret_cast<uintptr_t>(p) & 15) == 0 && (ld * (int64_t)sizeof(T)) % 16 == 0;
+}
+
+template <typename T>
+__device__ __forceinline__ void load4(const T* p, bool vec, int64_t valid, T (&v)[4]) {
+  if (vec && valid >= 4) {
+    if constexpr (sizeof(T) == 4) {
+      const float4 f = *reinterpret_cast<const float4*>(p);
+      v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
+    } else {
+      const double2 a = *reinterpret_cast<const double2*>(p);
+      const double2 b = *reinterpret_cast<const double2*>(p + 2);
+      v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) v[e] = e < valid ? p[e] : T(0);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void store4(T* p, bool vec, int64_t valid, const T (&v)[4]) {
+  if (vec && valid >= 4) {
+    if constexpr (sizeof(T) == 4) {
+      *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+      *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+      *reinterpret_cast<double2*>(p + 2) = make_double2(v[2], v[3]);
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      if (e < valid) p[e] = v[e];
+  }
+}
+
+inline unsigned sweep_blocks(int64_t units) {
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(units, 256 * kUnroll), 152 * 16));
+}
+
 template <typename Tdst, typename Tsrc>
-__global__ void copy2d_kernel(Tdst* dst, int64_t ldd, const Tsrc* src, int64_t lds, int64_t rows,
-                              int64_t cols, int64_t pad_to) {
-  for (int64_t i = blockIdx.y; i < rows; i += gridDim.y)
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < pad_to;
-         j += (int64_t)gridDim.x * blockDim.x)
-      dst[i * ldd + j] = j < cols ? (Tdst)src[i * lds + j] : (Tdst)0;
+__global__ void __launch_bounds__(256) copy2d_kernel(Tdst* dst, int64_t ldd, const Tsrc* src, int64_t lds,
+                                                     int64_t rows, int64_t cols, int64_t pad_to) {
+  const bool vs = aligned_rows(src, lds), vd = aligned_rows(dst, ldd);
+  const int64_t cpr = (pad_to + 3) / 4, units = rows * cpr;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t u0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u0 < units; u0 += stride * kUnroll) {
+    Tsrc v[kUnroll][4];
+#pragma unroll
+    for (int k = 0; k < kUnroll; ++k) {
+      const int64_t u = u0 + k * stride;
+      if (u < units) {
+        const int64_t i = u / cpr, j = (u % cpr) * 4;
+        load4<Tsrc>(src + i * lds + j, vs, cols - j, v[k]);  // zero beyond cols
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kUnroll; ++k) {
+      const int64_t u = u0 + k * stride;
+      if (u < units) {
+        const int64_t i = u / cpr, j = (u % cpr) * 4;
+        Tdst w[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) w[e] = (Tdst)v[k][e];
+        store4<Tdst>(dst + i * ldd + j, vd, pad_to - j, w);
+      }
+    }
+  }
 }
 
 template <typename Tdst, typename Tsrc>
 kf_status copy2d(cudaStream_t s, Tdst* dst, int64_t ldd, const Tsrc* src, int64_t lds, int64_t rows,
                  int64_t cols, bool zero_pad) {
   if (rows <= 0 || cols <= 0) return KF_OK;
-  int64_t pad_to = zero_pad ? ldd : cols;
-  dim3 grid((unsigned)std::min<int64_t>(ceil_div(pad_to, 256), 64), (unsigned)std::min<int64_t>(rows, 65535));
-  copy2d_kernel<Tdst, Tsrc><<<grid, 256, 0, s>>>(dst, ldd, src, lds, rows, cols, pad_to);
+  const int64_t pad_to = zero_pad ? ldd : cols;
+  copy2d_kernel<Tdst, Tsrc><<<sweep_blocks(rows * ((pad_to + 3) / 4)), 256, 0, s>>>(dst, ldd, src, lds, rows, cols,
+                                                                                     pad_to);
   note_launch();
   return launch_check("copy2d");
 }
 
 template <typename Tdst, typename Tsrc>
-__global__ void add_cov_kernel(Tdst* dst, int64_t ldd, const Tsrc* src, int64_t lds, int64_t n, int kind,
-                               const double* q) {
-  for (int64_t i = blockIdx.y; i < n; i += gridDim.y)
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
-      dst[i * ldd + j] = (Tdst)((double)src[i * lds + j] + cov_value(kind, q, n, i, j));
+__global__ void __launch_bounds__(256) add_cov_kernel(Tdst* dst, int64_t ldd, const Tsrc* src, int64_t lds,
+                                                      int64_t n, int kind, const double* q) {
+  const bool vs = aligned_rows(src, lds), vd = aligned_rows(dst, ldd);
+  const int64_t cpr = (n + 3) / 4, units = n * cpr;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t u0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u0 < units; u0 += stride * kUnroll) {
+    Tsrc v[kUnroll][4];
+#pragma unroll
+    for (int k = 0; k < kUnroll; ++k) {
+      const int64_t u = u0 + k * stride;
+      if (u < units) {
+        const int64_t i = u / cpr, j = (u % cpr) * 4;
+        load4<Tsrc>(src + i * lds + j, vs, n - j, v[k]);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kUnroll; ++k) {
+      const int64_t u = u0 + k * stride;
+      if (u < units) {
+        const int64_t i = u / cpr, j = (u % cpr) * 4;
+        Tdst w[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) w[e] = (Tdst)((double)v[k][e] + cov_value(kind, q, n, i, j + e));
+        store4<Tdst>(dst + i * ldd + j, vd, n - j, w);
+      }
+    }
+  }
 }
 
 template <typename Tdst, typename Tsrc>
 kf_status add_cov(cudaStream_t s, Tdst* dst, int64_t ldd, const Tsrc* src, int64_t lds, int64_t n,
                   int q_kind, const double* q) {
   if (n <= 0) return KF_OK;
-  dim3 grid((unsigned)std::min<int64_t>(ceil_div(n, 256), 64), (unsigned)std::min<int64_t>(n, 65535));
-  add_cov_kernel<Tdst, Tsrc><<<grid, 256, 0, s>>>(dst, ldd, src, lds, n, q_kind, q);
+  add_cov_kernel<Tdst, Tsrc><<<sweep_blocks(n * ((n + 3) / 4)), 256, 0, s>>>(dst, ldd, src, lds, n, q_kind, q);
   note_launch();
   return launch_check("add_cov");
 }
 
-// one warp per row, float64 accumulation
+// one warp per row, float64 accumulation; each lane reads 4 consecutive
+// elements per step (16-byte loads for aligned float32 rows)
 template <typename T>
 __global__ void gemv_kernel(int64_t rows, int64_t cols, const T* A, int64_t lda, const double* x,
                             const double* ybase, double sign, double* y) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const bool vec = aligned_rows(A, lda);
   for (int64_t i = warp; i < rows; i += nwarps) {
+    const T* row = A + i * lda;
     double acc = 0.0;
-    for (int64_t j = lane; j < cols; j += 32) acc = fma((double)A[i * lda + j], x[j], acc);
+    for (int64_t j = 4 * lane; j < cols; j += 128) {
+      T a[4];
+      load4<T>(row + j, vec, cols - j, a);
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        if (j + e < cols) acc = fma((double)a[e], x[j + e], acc);
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) y[i] = ybase ? ybase[i] + sign * acc : acc;

@@ -17,7 +17,8 @@
 // 2.33 N^3 flops), in exchange for large, fully parallel products only.
 // With F = I and a scalar or diagonal Q the gain needs no product with
 // P_{t|t} at all: J_t = P_{t|t} (P_{t|t} + Q)^{-1} = I - Q P_{t+1|t}^{-1}, and
-// P_{t+1|t}^{-1} = W^T W costs N^3 / 3 (gain_identity_tc).
+// P_{t+1|t}^{-1} = W^T W costs N^3 / 3 and the gain is formed in the product's
+// epilogue (gain_identity_tc).
 #include <set>
 #include <utility>
 
@@ -160,30 +161,19 @@ kf_status gain_from_inverse_tc(cudaStream_t s, TcScratch& sc, int n, const float
   return tc_gemm_split(s, sc, b, 3, false);
 }
 
-__global__ void gain_identity_kernel(int64_t n, const float* Pinv, int64_t ldp, int q_kind, const double* q, float* J,
-                                     int64_t ldj) {
-  for (int64_t i = blockIdx.y; i < n; i += gridDim.y) {
-    const float qi = (float)(q_kind == 0 ? q[0] : q[i]);
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
-      J[i * ldj + j] = (i == j ? 1.0f : 0.0f) - qi * Pinv[i * ldp + j];
-  }
-}
-
 kf_status gain_identity_tc(cudaStream_t s, TcScratch& sc, int n, const float* W, int64_t ldw, int q_kind,
-                           const double* q, float* Pinv, int64_t ldp, float* J, int64_t ldj, int* status) {
+                           const double* q, float* J, int64_t ldj, int* status) {
   if (q_kind != 0 && q_kind != 1) return KF_ERR_ARG;
-  GemmParams<float> g;  // P_{t+1|t}^{-1} = W^T W, lower triangle computed and mirrored
+  GemmParams<float> g;  // J = I - Q (W^T W): lower triangle computed, the upper one mirrored with q_j
   g.M = n; g.N = n; g.K = n;
-  g.out = Pinv; g.ldo = ldp;
+  g.out = J; g.ldo = ldj;
+  g.gain_q = q;
+  g.gain_q_kind = q_kind;
   g.sym = 1;
   g.tri_a = -1;  // row r of W^T is zero for k < r
   g.tri_b = -1;
   g.status = status;
-  KF_TRY(tc_gemm_ops(s, sc, TcOperand{W, ldw, 0, 1}, TcOperand{W, ldw, 0, 1}, g, 3));
-  dim3 grid((unsigned)std::min<int64_t>(ceil_div(n, 256), 64), (unsigned)std::min<int64_t>(n, 65535));
-  gain_identity_kernel<<<grid, 256, 0, s>>>(n, Pinv, ldp, q_kind, q, J, ldj);
-  note_launch();
-  return launch_check("gain_identity");
+  return tc_gemm_ops(s, sc, TcOperand{W, ldw, 0, 1}, TcOperand{W, ldw, 0, 1}, g, 3);
 }
 
 }  // namespace kfm

@@ -18,8 +18,9 @@ kf_status gain_from_inverse_tc(cudaStream_t s, TcScratch& sc, int n, const float
 
 // F = I with Q = q I or diagonal: J = P_{t|t} (P_{t|t} + Q)^{-1} = I - Q P_{t+1|t}^{-1},
 // with P_{t+1|t}^{-1} = W^T W formed on the lower triangle (n^3 / 3 instead of
-// the 2 n^3 of the two triangular products).  Pinv is n x n scratch.
+// the 2 n^3 of the two triangular products); J is written by that product's
+// epilogue, so P_{t+1|t}^{-1} itself is never stored.
 kf_status gain_identity_tc(cudaStream_t s, TcScratch& sc, int n, const float* W, int64_t ldw, int q_kind,
-                           const double* q, float* Pinv, int64_t ldp, float* J, int64_t ldj, int* status);
+                           const double* q, float* J, int64_t ldj, int* status);
 
 }  // namespace kfm
