@@ -19,8 +19,11 @@
 //           stage's "empty" mbarrier, which hands the stage back to the TMA
 //           lane when the MMAs have read it; at the end it commits to the
 //           "accumulator ready" barrier;
-//   warps 2-5  read the accumulator with tcgen05.ld (each warp its 32 TMEM
-//           lanes = 32 rows) and apply the covariance epilogue.
+//   warps 2-9  read the accumulator with tcgen05.ld (each warp its 32 TMEM
+//           lanes = 32 rows, half of the columns), promote it into float32
+//           registers after every k-tile, and at the end stage the tile in
+//           shared memory and apply the covariance epilogue in coalesced row
+//           and (for mirrored symmetric outputs) column sweeps.
 // Every mbarrier wait is bounded (about 2 s of %globaltimer); on expiry the
 // kernel raises KF_ERR_TIMEOUT in the status word, stops issuing, waits
 // (bounded) for what it already issued, frees TMEM and returns.
@@ -313,12 +316,63 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       __syncwarp();
       if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(acce_bar(buf)) : "memory");
     }
-    if (ok && gi < p.M) {
+    // Stage the tile in shared memory (the operand stages are idle once the
+    // last chunk has been promoted), one column half at a time, then sweep it
+    // by rows for the direct outputs and by columns for the mirrored ones, so
+    // that every global access of a warp covers consecutive addresses.
+    constexpr int PITCH = HALF + 1;  // odd pitch: row and column sweeps are both conflict-free
+    static_assert((size_t)BM * PITCH * sizeof(TE) <= (size_t)C::STAGES * C::STAGE_BYTES, "tile fits the stages");
+    TE* tile = reinterpret_cast<TE*>(gbase);
+    const int ew = warp - 2;  // epilogue warp 0..7
+    for (int hh = 0; hh < 2; ++hh) {
+      if (ok && h == hh) {
+        const int r = 32 * q + lane;
 #pragma unroll
-      for (int j = 0; j < HALF; ++j) {
-        const int gj = n0 + h * HALF + j;
-        if (gj < p.N && !(p.sym && gj > gi)) epilogue_store(p, gi, gj, (TE)acc[j]);
+        for (int j = 0; j < HALF; ++j) tile[r * PITCH + j] = (TE)acc[j];
       }
+      asm volatile("bar.sync 1, 256;" ::: "memory");
+      const bool go = !*abort_flag;
+      const int c0 = n0 + hh * HALF;
+      if (go) {
+        // row sweep: lane -> column, warp -> rows ew, ew + 8, ...; the cin / csub
+        // values of EB elements are loaded before any of them is stored (cin
+        // may be the output array, so the compiler would not hoist them)
+        constexpr int CPL = HALF / 32, PER = (BM / 8) * CPL, EB = HALF >= 128 ? 4 : 8;
+        static_assert(PER % EB == 0, "whole batches");
+        for (int b0 = 0; b0 < PER; b0 += EB) {
+          TE cv[EB], sv[EB];
+#pragma unroll
+          for (int k = 0; k < EB; ++k) {
+            const int e = b0 + k, r = ew + 8 * (e / CPL), cc = lane + 32 * (e % CPL);
+            const int gi2 = m0 + r, gj = c0 + cc;
+            const bool valid = gi2 < p.M && gj < p.N && !(p.sym && gj > gi2);
+            cv[k] = (valid && p.cin) ? p.cin[(int64_t)gi2 * p.ldcin + gj] : TE(0);
+            sv[k] = (valid && p.csub) ? p.csub[(int64_t)gi2 * p.ldcsub + gj] : TE(0);
+          }
+#pragma unroll
+          for (int k = 0; k < EB; ++k) {
+            const int e = b0 + k, r = ew + 8 * (e / CPL), cc = lane + 32 * (e % CPL);
+            const int gi2 = m0 + r, gj = c0 + cc;
+            if (gi2 < p.M && gj < p.N && !(p.sym && gj > gi2))
+              tile[r * PITCH + cc] = epilogue_row(p, gi2, gj, tile[r * PITCH + cc], cv[k], sv[k]);
+          }
+        }
+      }
+      if (p.sym == 1) {
+        asm volatile("bar.sync 1, 256;" ::: "memory");
+        if (go && m0 + BM - 1 > c0) {  // the half has elements strictly below the diagonal
+          for (int c = ew; c < HALF; c += 8) {
+            const int gj = c0 + c;
+            if (gj >= p.N) break;
+            for (int r = lane; r < BM; r += 32) {
+              const int gi2 = m0 + r;
+              if (gi2 >= p.M || gi2 <= gj) continue;
+              epilogue_mirror(p, gj, gi2, tile[r * PITCH + c]);
+            }
+          }
+        }
+      }
+      asm volatile("bar.sync 1, 256;" ::: "memory");  // the tile is rewritten by the next half
     }
   }
   // every issued MMA must have finished before TMEM is freed
