@@ -294,9 +294,9 @@ def main():
                 "FP64 nominal 1.25 TFLOP/s"}
     avg_s = ms_l / 1e3 / max(n_l, 1)
     achieved = smoother_gemm_flops_per_launch(N) / avg_s / 1e12
-    # DRAM bytes of one launch of that kernel (dram__bytes_read.sum + dram__bytes_write.sum from an ncu
-    # capture of the current kernel); None until captured
-    traffic = None
+    # DRAM bytes of one launch of that kernel at N = 8196 (dram__bytes_read.sum + dram__bytes_write.sum,
+    # one ncu --set full capture of W = J D at t = 2 of the T = 3 run: 4.280e9 read + 0.278e9 written)
+    traffic = 4.557e9 if args.prec == "mixed" and prof[7][0] > 0 and N == 8196 else None
     roof.update({"kernel": kname, "achieved": achieved, "frac": achieved / roof["peak"], "traffic": traffic,
                  "peak_source": peak_src, "launches": n_l, "avg_launch_ms": avg_s * 1e3,
                  "work_per_launch": "(2 N^3 + N^2 (N+1)) / 2 flops, N = 8196"})

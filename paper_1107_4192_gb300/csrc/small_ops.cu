@@ -123,8 +123,12 @@ __global__ void __launch_bounds__(256) add_cov_kernel(Tdst* dst, int64_t ldd, co
       if (u < units) {
         const int64_t i = u / cpr, j = (u % cpr) * 4;
         Tdst w[4];
+        // Q is zero off the diagonal unless dense: there the sum is the value itself
+        // (float64 arithmetic is a small fraction of float32's on this part, so it is
+        // spent only where Q adds something)
 #pragma unroll
-        for (int e = 0; e < 4; ++e) w[e] = (Tdst)((double)v[k][e] + cov_value(kind, q, n, i, j + e));
+        for (int e = 0; e < 4; ++e)
+          w[e] = (kind == 2 || i == j + e) ? (Tdst)((double)v[k][e] + cov_value(kind, q, n, i, j + e)) : (Tdst)v[k][e];
         store4<Tdst>(dst + i * ldd + j, vd, n - j, w);
       }
     }
