@@ -328,6 +328,8 @@ def main():
         line["serve"] = serving_sample(args, B, synth)
     if rank == 0 and world == 1 and not args.no_fp64_plain and args.prec != "fp64":
         line["fp64_plain"] = fp64_plain_prefix(prob, B, solver, synth, torch)
+    if rank == 0 and world == 1:
+        line["mne_init"] = mne_init_sample(prob, B, solver, torch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         per, sample = cpu_oracle_timestep(synth.config2(T=2))
         line["cpu_baseline"] = {"value": 1.0 / per, "unit": "timesteps/s", "cores": host_threads(), "kind": "oracle",
@@ -363,6 +365,26 @@ def batched_sample(args, B, synth):
     summ["epochs_per_s"] = summ["completed"] / summ["wall_s"] if summ["wall_s"] > 0 else 0.0
     summ["sample"] = f"{len(probs)} epochs, 8 concurrent plans on separate streams"
     return summ
+
+
+def mne_init_sample(prob, B, solver, torch):
+    """The paper's initialisation (x0 = minimum-norm estimate, Q = sample covariance of the
+    differenced estimates) on the whole workload: one call after one warm-up call."""
+    h = solver.host_inputs(prob)
+    t = lambda a: torch.from_numpy(a).cuda()
+    H, R, Y, C = t(h["H"]), t(h["R"]), t(h["Y"]), t(np.array([1.0]))
+    x0 = torch.empty(prob.N, dtype=torch.float64, device="cuda")
+    Q = torch.empty(prob.N, prob.N, dtype=torch.float64, device="cuda")
+    args = (H, C, 0, R, h["r_kind"], Y, prob.N, prob.m, prob.T, 1.0, None, x0, Q)
+    B.mne_init(*args)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    B.mne_init(*args)
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t0) * 1e3
+    del Q
+    return {"ms": ms, "sample": f"x0 and dense Q from the {prob.T} float64 minimum-norm estimates (C = I, "
+                                f"lambda = 1), N = {prob.N}, m = {prob.m}; includes its own allocations"}
 
 
 def fp64_plain_prefix(prob, B, solver, synth, torch, T_pre=3):

@@ -151,6 +151,25 @@ kf_status mne_solve(const double* H, const double* C, int32_t c_kind,
                     int64_t N, int64_t m, int64_t T, double lambda,
                     double* X_out, void* stream);
 
+/* The paper's initialisation (Sec. 2.4, practical considerations): the
+ * initial state is the minimum-norm estimate, and the state-noise covariance
+ * Sigma_w (Q here) is the sample covariance of the differenced sequence of
+ * minimum-norm estimates X[0..T-1] (eqn 5, as mne_solve):
+ *   x0_out = X[0]   (the first sample's estimate: no observation exists at t = 0)
+ *   d_k    = X[k+1] - X[k],  k = 0..T-2
+ *   Q_out  = sum_k (d_k - dbar)(d_k - dbar)^T / (T - 2),  dbar = mean of d_k
+ * (unbiased, mean removed; rank <= T - 2, so Q_out is singular when T - 2 < N
+ * and goes to kf_filter as a dense Q, where P_{t|t} + Q stays positive
+ * definite).  Arguments as for mne_solve, plus:
+ *   X_out:  T x N output of the estimates, or NULL (then kept internally);
+ *   x0_out: N output; Q_out: N x N output, row-major, exactly symmetric.
+ * Needs T >= 3 (KF_ERR_ARG otherwise).  float64 throughout; device pointers;
+ * uses its own temporary device memory. */
+kf_status mne_init(const double* H, const double* C, int32_t c_kind,
+                   const double* R, int32_t r_kind, const double* Y,
+                   int64_t N, int64_t m, int64_t T, double lambda,
+                   double* X_out, double* x0_out, double* Q_out, void* stream);
+
 /* Host-buffer convenience: copies the HOST inputs to plan-owned device
  * buffers, runs kf_filter then fis_smooth, and copies the HOST outputs back.
  * Argument meaning as for kf_filter / fis_smooth (all pointers here are host

@@ -29,12 +29,18 @@ or silent at these points):
   starting from the filter's last step.
 * The covariance update of eqn 10 (I - K H) P is computed in Joseph form
   and symmetrised; both are equal in exact arithmetic.
+* Initialisation (Sec. 2.4): the initial state "J_0^MNE" is read as the
+  minimum-norm estimate of the first sample, and Sigma_w as the unbiased
+  sample covariance (mean removed, divisor T - 2) of the T - 1 differences
+  of consecutive minimum-norm estimates.
 
 Parity pins (checked by the CPU test-suite, not by this module): the MNE
 closed form of eqn 5 solved as the regularised least squares of eqn 4,
 the brute-force joint Gaussian posterior, the scalar Riccati fixed point,
 an information-form filter, symmetry / PSD / Loewner ordering and special
-cases.  Every function here is pinned by at least one of them.
+cases; for mne_init, the sample covariance of known random-walk increments
+(accumulated one sample at a time) and invariance to a constant shift.
+Every function here is pinned by at least one of them.
 """
 from __future__ import annotations
 
@@ -146,6 +152,19 @@ def mne_solve(H, C, R, Y, lam=1.0):
     Z = sla.solve_triangular(L, Y.T, lower=True)
     W = sla.solve_triangular(L.T, Z, lower=False)
     return (lam * (C @ H.T) @ W).T
+
+
+def mne_init(H, C, R, Y, lam=1.0):
+    """The paper's initialisation (Sec. 2.4): the initial state is the minimum-norm
+    estimate and Sigma_w (Q) is the sample covariance of the differenced sequence
+    of minimum-norm estimates.  Readings: the initial state is the first sample's
+    estimate (no observation exists at t = 0); the sample covariance removes the
+    mean of the differences and divides by (number of differences - 1)."""
+    X = mne_solve(H, C, R, Y, lam)
+    d = X[1:] - X[:-1]
+    dc = d - d.mean(axis=0)
+    Q = dc.T @ dc / (d.shape[0] - 1)
+    return X[0].copy(), symmetrise(Q), X
 
 
 # ------------------------------------- second, independent recursion

@@ -56,6 +56,7 @@ _SIGS = {
     "kf_filter": (ctypes.c_int, [_P] * 12 + [ctypes.POINTER(_I64)]),
     "fis_smooth": (ctypes.c_int, [_P, _P, _P, _P, _I64, ctypes.POINTER(_I64)]),
     "mne_solve": (ctypes.c_int, [_P, _P, _I32, _P, _I32, _P, _I64, _I64, _I64, _D, _P, _P]),
+    "mne_init": (ctypes.c_int, [_P, _P, _I32, _P, _I32, _P, _I64, _I64, _I64, _D, _P, _P, _P, _P]),
     "kf_solve_host": (ctypes.c_int, [_P] * 14 + [ctypes.POINTER(_I64)]),
     "kf_plan_profile": (ctypes.c_int, [_P, _I32]),
     "kf_plan_profile_read": (ctypes.c_int, [_P, _I32, ctypes.POINTER(_I64), ctypes.POINTER(_D)]),
@@ -173,6 +174,13 @@ def mne_solve(H, C, c_kind, R, r_kind, Y, N, m, T, lam, X_out, stream=None):
     st = lib().mne_solve(_f64(H), _f64(C), c_kind, _f64(R), r_kind, _f64(Y), N, m, T, lam, _f64(X_out),
                          _stream(stream))
     _check(st, "mne_solve")
+
+
+def mne_init(H, C, c_kind, R, r_kind, Y, N, m, T, lam, X_out, x0_out, Q_out, stream=None):
+    st = lib().mne_init(_f64(H), _f64(C), c_kind, _f64(R), r_kind, _f64(Y), N, m, T, lam,
+                        _f64(X_out) if X_out is not None else None, _f64(x0_out), _f64(Q_out),
+                        _stream(stream))
+    _check(st, "mne_init")
 
 
 def _hp(a):

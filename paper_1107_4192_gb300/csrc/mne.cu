@@ -3,6 +3,9 @@
 // factored by the same blocked Cholesky as S_t; W = Y G^{-1} is two right-side
 // triangular solves; X = lambda W H C is one product (plus a column scaling
 // when C is diagonal).
+//
+// mne_init: the paper's initialisation from these estimates (Sec. 2.4):
+// x0 = X[0] and Q = the sample covariance of the differences X[k+1] - X[k].
 #include <vector>
 
 #include "ops.cuh"
@@ -102,4 +105,47 @@ extern "C" kf_status mne_solve(const double* H, const double* C, int32_t c_kind,
   KF_CUDA_TRY(cudaMemcpyAsync(h, st, sizeof(h), cudaMemcpyDeviceToHost, s));
   KF_CUDA_TRY(cudaStreamSynchronize(s));
   return (kf_status)h[ST_CODE];
+}
+
+namespace {
+
+// Dt[i][k] = (X[k+1][i] - X[k][i]) - dbar_i for k < T - 1, where the mean of the
+// differences telescopes to dbar_i = (X[T-1][i] - X[0][i]) / (T - 1).
+__global__ void centred_differences_kernel(int64_t N, int64_t T, const double* X, double* Dt) {
+  const int64_t K = T - 1;
+  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < N * K; u += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = u / N, i = u % N;  // consecutive threads read consecutive sources of one row
+    const double dbar = (X[(T - 1) * N + i] - X[i]) / (double)K;
+    Dt[i * K + k] = (X[(k + 1) * N + i] - X[k * N + i]) - dbar;
+  }
+}
+
+}  // namespace
+
+extern "C" kf_status mne_init(const double* H, const double* C, int32_t c_kind, const double* R, int32_t r_kind,
+                              const double* Y, int64_t N, int64_t m, int64_t T, double lambda, double* X_out,
+                              double* x0_out, double* Q_out, void* stream) {
+  if (!x0_out || !Q_out || T < 3 || N < 1 || N > INT32_MAX) return KF_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  Tmp tmp;
+  double* X = X_out;
+  if (!X) KF_TRY(tmp.get(&X, (size_t)T * N));
+  KF_TRY(mne_solve(H, C, c_kind, R, r_kind, Y, N, m, T, lambda, X, stream));
+  KF_CUDA_TRY(cudaMemcpyAsync(x0_out, X, (size_t)N * 8, cudaMemcpyDeviceToDevice, s));
+  double* Dt;
+  KF_TRY(tmp.get(&Dt, (size_t)N * (T - 1)));
+  const unsigned blocks = (unsigned)std::min<int64_t>(ceil_div(N * (T - 1), 256), 152 * 16);
+  centred_differences_kernel<<<blocks, 256, 0, s>>>(N, T, X, Dt);
+  note_launch();
+  KF_TRY(launch_check("centred_differences"));
+  GemmParams<double> g;  // Q = Dt Dt^T / (T - 2), lower triangle computed and mirrored
+  g.M = (int)N; g.N = (int)N; g.K = (int)(T - 1);
+  g.A = Dt; g.lda = T - 1;
+  g.B = Dt; g.ldb = T - 1;
+  g.alpha = 1.0 / (double)(T - 2);
+  g.out = Q_out; g.ldo = N;
+  g.sym = 1;
+  KF_TRY(gemm_simt<double>(s, true, g));
+  KF_CUDA_TRY(cudaStreamSynchronize(s));
+  return KF_OK;
 }

@@ -153,6 +153,56 @@ def test_mne_solve(c_kind, lam):
     assert rel_err_per_step(X.cpu().numpy(), ref) <= 1e-11
 
 
+@pytest.mark.parametrize("c_kind", [0, 1, 2])
+@pytest.mark.parametrize("N,m,T", [(230, 37, 9), (129, 20, 3)])
+def test_mne_init(c_kind, N, m, T):
+    """Sec. 2.4 initialisation (x0 and Q from the minimum-norm estimates) against the oracle;
+    then used as x0 and dense Q of a float64 filter + smoother run, also against the oracle."""
+    rng = np.random.default_rng(6 + c_kind)
+    H = synth.lead_field(rng, m, N)
+    Y = rng.standard_normal((T, m))
+    Rv = rng.uniform(0.5, 2, m)
+    Cv = {0: np.array([0.7]), 1: rng.uniform(0.5, 2, N)}.get(c_kind)
+    if c_kind == 2:
+        A = rng.standard_normal((N, N)) / np.sqrt(N)
+        Cv = 0.5 * np.eye(N) + A @ A.T
+    Cd = ko.dense_cov(c_kind, Cv, N)
+    x0_ref, Q_ref, X_ref = ko.mne_init(H, Cd, np.diag(Rv), Y, 1.5)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float64)).cuda()
+    x0 = torch.empty(N, dtype=torch.float64, device="cuda")
+    Q = torch.empty(N, N, dtype=torch.float64, device="cuda")
+    X = torch.empty(T, N, dtype=torch.float64, device="cuda")
+    B.mne_init(t(H), t(Cv), c_kind, t(Rv), B.KF_COV_DIAG, t(Y), N, m, T, 1.5, X, x0, Q)
+    assert rel_err_per_step(X.cpu().numpy(), X_ref) <= 1e-11
+    assert np.linalg.norm(x0.cpu().numpy() - x0_ref) <= 1e-11 * np.linalg.norm(x0_ref)
+    Qg = Q.cpu().numpy()
+    assert np.array_equal(Qg, Qg.T)
+    assert np.linalg.norm(Qg - Q_ref) <= 1e-10 * np.linalg.norm(Q_ref)
+    # without X_out
+    Q2 = torch.empty(N, N, dtype=torch.float64, device="cuda")
+    B.mne_init(t(H), t(Cv), c_kind, t(Rv), B.KF_COV_DIAG, t(Y), N, m, T, 1.5, None, x0, Q2)
+    assert torch.equal(Q, Q2)
+
+
+def test_mne_init_feeds_the_filter():
+    """x0 and dense Q from mne_init drive a float64 KF + FIS on the GPU, checked against the
+    oracle run from the oracle's own initialisation (the paper's pipeline, Sec. 2.4)."""
+    prob = synth.mesh_problem(200, 30, 12, seed=9)
+    F, _, H, R, P0 = oracle_dense(prob)
+    x0_ref, Q_ref, _ = ko.mne_init(H, np.eye(prob.N), R, prob.Y, 1.0)
+    ref = ko.kf_fis(F, Q_ref, H, R, prob.Y, x0_ref, P0)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float64)).cuda()
+    x0 = torch.empty(prob.N, dtype=torch.float64, device="cuda")
+    Q = torch.empty(prob.N, prob.N, dtype=torch.float64, device="cuda")
+    B.mne_init(t(prob.H), t(np.array([1.0])), 0, t(prob.R), B.KF_COV_DIAG, t(prob.Y), prob.N, prob.m, prob.T,
+               1.0, None, x0, Q)
+    prob.x0 = x0.cpu().numpy()
+    prob.q_kind, prob.Q = 2, Q.cpu().numpy()
+    out = solver.run(prob, prec=B.KF_PREC_FP64)
+    assert rel_err_per_step(out["x_filt"], ref["x_filt"]) <= 1e-9
+    assert rel_err_per_step(out["x_smooth"], ref["x_smooth"]) <= 1e-9
+
+
 def test_not_pd_innovation_is_reported():
     """R = 0 with a rank-deficient H: S_1 is singular -> KF_ERR_NOT_PD at step 1."""
     prob = synth.random_walk_problem(40, 6, 3, seed=1)

@@ -79,6 +79,55 @@ def test_mne_solve_matches_least_squares(lam):
         assert np.linalg.norm(X[t] - x_ls) <= 1e-12 * np.linalg.norm(x_ls)
 
 
+def _running_sample_cov(samples):
+    """Unbiased sample covariance accumulated one sample at a time (Welford's update)."""
+    n = 0
+    mean = np.zeros(samples.shape[1])
+    m2 = np.zeros((samples.shape[1], samples.shape[1]))
+    for s in samples:
+        n += 1
+        delta = s - mean
+        mean = mean + delta / n
+        m2 = m2 + np.outer(delta, s - mean)
+    return m2 / (n - 1)
+
+
+def test_mne_init_recovers_known_increments():
+    """Sec. 2.4 initialisation: with H = I, a tiny R and an exact random walk as data, the
+    minimum-norm estimates are the walk itself, so x0 is its first sample and Q is the sample
+    covariance of its known increments (accumulated by a different route)."""
+    rng = np.random.default_rng(11)
+    N, T = 6, 40
+    steps = rng.standard_normal((T - 1, N)) @ np.diag([0.5, 1.0, 2.0, 0.3, 1.5, 0.8])
+    walk = np.vstack([rng.standard_normal(N), np.zeros((T - 1, N))])
+    walk[1:] = walk[0] + np.cumsum(steps, axis=0)
+    x0, Q, X = ko.mne_init(np.eye(N), np.eye(N), 1e-13 * np.eye(N), walk, lam=1.0)
+    assert np.allclose(X, walk, rtol=0, atol=1e-9)
+    assert np.allclose(x0, walk[0], rtol=0, atol=1e-9)
+    ref = _running_sample_cov(steps)
+    assert np.linalg.norm(Q - ref) <= 1e-9 * np.linalg.norm(ref)
+
+
+def test_mne_init_structure_and_shift_invariance():
+    """Q is symmetric, positive semidefinite, of rank <= T - 2, and unchanged when every
+    observation moves by the same H c (the estimates then move by one constant vector)."""
+    rng = np.random.default_rng(12)
+    N, m, T = 25, 8, 7
+    H = synth.lead_field(rng, m, N)
+    C = np.diag(rng.uniform(0.5, 2.0, N))
+    R = np.diag(rng.uniform(0.5, 2.0, m))
+    Y = rng.standard_normal((T, m))
+    x0, Q, X = ko.mne_init(H, C, R, Y, lam=2.0)
+    assert np.array_equal(Q, Q.T)
+    ev = np.linalg.eigvalsh(Q)
+    assert ev.min() >= -1e-12 * ev.max()
+    assert np.sum(ev > 1e-10 * ev.max()) <= T - 2
+    assert np.array_equal(x0, X[0])
+    c = rng.standard_normal(N)
+    _, Q2, _ = ko.mne_init(H, C, R, Y + H @ c, lam=2.0)
+    assert np.linalg.norm(Q2 - Q) <= 1e-10 * np.linalg.norm(Q)
+
+
 # ------------------------------------------------- brute-force posterior
 
 def _tiny_general(seed=7, N=4, m=3, T=6):

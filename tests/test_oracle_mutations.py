@@ -35,6 +35,9 @@ MUTATIONS = [
      "Ps[t] = symmetrise(Pf[t] - J @ (Ps[t + 1] - Pp[t + 1]) @ J.T)"),
     ("posterior cross-cov transposed", "blk = F @ blk", "blk = F.T @ blk"),
     ("mne missing lambda in G", "G = lam * (H @ C @ H.T) + R", "G = (H @ C @ H.T) + R"),
+    ("init covariance divisor n", "Q = dc.T @ dc / (d.shape[0] - 1)", "Q = dc.T @ dc / d.shape[0]"),
+    ("init covariance without mean removal", "dc = d - d.mean(axis=0)", "dc = d"),
+    ("init state from the last estimate", "return X[0].copy(), symmetrise(Q), X", "return X[-1].copy(), symmetrise(Q), X"),
 ]
 
 
@@ -74,6 +77,15 @@ def _pins_pass(mod) -> bool:
     lam = 3.0
     ref = np.stack([eqn4_minimiser(Hm, Rm, y, np.zeros(12), lam * C)[0] for y in Y])
     ok &= np.allclose(mod.mne_solve(Hm, C, Rm, Y, lam), ref, rtol=1e-12, atol=1e-14)
+    # initialisation pin: known random-walk increments (see test_oracle)
+    from tests.test_oracle import _running_sample_cov
+    rng = np.random.default_rng(11)
+    steps = rng.standard_normal((20, 4))
+    walk = np.vstack([rng.standard_normal(4), np.zeros((20, 4))])
+    walk[1:] = walk[0] + np.cumsum(steps, axis=0)
+    x0, Qi, _ = mod.mne_init(np.eye(4), np.eye(4), 1e-13 * np.eye(4), walk, lam=1.0)
+    ok &= np.allclose(x0, walk[0], rtol=0, atol=1e-9)
+    ok &= np.allclose(Qi, _running_sample_cov(steps), rtol=1e-9, atol=1e-12)
     return bool(ok)
 
 
