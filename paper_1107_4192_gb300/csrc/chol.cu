@@ -353,7 +353,7 @@ kf_status potrf_diag(cudaStream_t s, T* A, int64_t lda, int n, T* dinv, int64_t 
 
 template <typename T>
 kf_status potrf(cudaStream_t s, T* A, int64_t lda, int n, T* dinv, int nb, int* status, int step) {
-  if (nb != potrf_block<T>()) return KF_ERR_ARG;
+  if (nb != potrf_block<T>() && nb != 32) return KF_ERR_ARG;  // 32: small matrices (more, cheaper leaves)
   for (int k = 0; k < n; k += nb) {
     const int kb = n - k < nb ? n - k : nb;
     T* Akk = A + (int64_t)k * lda + k;

@@ -1,6 +1,8 @@
 // CUDA-core (FMA) tiled GEMM for float64 and float32 with the fused
 // covariance epilogue of ops.cuh.  Used for every float64 product of the
 // plain path, the float32 path, and the blocked Cholesky / triangular solves.
+#include <utility>
+
 #include "epilogue.cuh"
 
 namespace kfm {
@@ -17,6 +19,13 @@ template <> struct SimtCfg<double> {
 template <> struct SimtCfg<float> {
   static constexpr int BM = 128, BN = 128, BK = 8, TM = 8, TN = 8, PAD = 4;
 };
+// float64 products too small to fill the GPU with 64 x 64 tiles (the m x m
+// innovation factorisation, its panels): the float64 pipe does about two
+// multiply-adds per clock per SM, so such a product is bound by how many SMs
+// it reaches.  16 x 16 tiles, one output per thread, same summation order.
+struct SimtCfgSmall64 {
+  static constexpr int BM = 16, BN = 16, BK = 16, TM = 1, TN = 1, PAD = 1;
+};
 
 // Maps a linear block index onto the lower-triangular tile (tm >= tn).
 __device__ __forceinline__ void tri_tile(int b, int& tm, int& tn) {
@@ -27,9 +36,8 @@ __device__ __forceinline__ void tri_tile(int b, int& tm, int& tn) {
   tn = b - r * (r + 1) / 2;
 }
 
-template <typename T, bool TB>
+template <typename T, bool TB, typename C = SimtCfg<T>>
 __global__ void __launch_bounds__(256) gemm_simt_kernel(GemmParams<T> p) {
-  using C = SimtCfg<T>;
   constexpr int BM = C::BM, BN = C::BN, BK = C::BK, TM = C::TM, TN = C::TN;
   constexpr int LDA_S = BM + C::PAD, LDB_S = BN + C::PAD;
   __shared__ __align__(16) T As[BK * LDA_S];
@@ -127,15 +135,58 @@ kf_status gemm_simt(cudaStream_t s, bool transB, const GemmParams<T>& p) {
     // aligned float32 operands take the pipelined kernel (same products, same order)
     if (gemm_small_ok(transB, p)) return gemm_small(s, transB, p);
   }
-  dim3 grid;
-  if (p.sym) {
-    if (p.M != p.N) return KF_ERR_ARG;
-    int64_t nt = ceil_div(p.M, C::BM);
-    grid = dim3((unsigned)(nt * (nt + 1) / 2));
-  } else {
-    grid = dim3((unsigned)ceil_div(p.N, C::BN), (unsigned)ceil_div(p.M, C::BM));
-    if (grid.y > 65535) return KF_ERR_ARG;
+  if (p.sym && p.M != p.N) return KF_ERR_ARG;
+  auto grid_for = [&](int bm, int bn) {
+    if (p.sym) {
+      const int64_t nt = ceil_div(p.M, bm);
+      return dim3((unsigned)(nt * (nt + 1) / 2));
+    }
+    return dim3((unsigned)ceil_div(p.N, bn), (unsigned)ceil_div(p.M, bm));
+  };
+  dim3 grid = grid_for(C::BM, C::BN);
+  if constexpr (sizeof(T) == 8) {
+    // Callers run in-place row transforms (out == A) that rely on one column tile
+    // owning all N <= 64 columns; the small tiles are used only when no output
+    // element is also an operand element.
+    // exact for two blocks of doubles with the same row stride (disjoint column or
+    // row ranges of one matrix), a byte-range test otherwise
+    auto apart = [](const void* a, size_t ea, int64_t la, int64_t ra, int64_t ca, const void* b, size_t eb,
+                    int64_t lb, int64_t rb, int64_t cb) {
+      if (!a || !b || ra <= 0 || ca <= 0 || rb <= 0 || cb <= 0) return true;
+      const char* a0 = static_cast<const char*>(a);
+      const char* b0 = static_cast<const char*>(b);
+      const char* a1 = a0 + ((ra - 1) * la + ca) * (int64_t)ea;
+      const char* b1 = b0 + ((rb - 1) * lb + cb) * (int64_t)eb;
+      if (a1 <= b0 || b1 <= a0) return true;
+      if (ea != eb || la != lb || la <= 0) return false;
+      const int64_t d = (b0 - a0) / (int64_t)ea;
+      if ((b0 - a0) % (int64_t)ea) return false;
+      const int64_t dr = d >= 0 ? d / la : -((-d + la - 1) / la), dc = d - dr * la;
+      if (dc + cb > la) return false;
+      return !(dr < ra && dr + rb > 0 && dc < ca && dc + cb > 0);
+    };
+    const int64_t rB = transB ? p.N : p.K, cB = transB ? p.K : p.N;
+    bool separate = true;
+    const void* outs[3] = {p.out, p.out2, p.outf};
+    const size_t es[3] = {sizeof(T), sizeof(T), sizeof(float)};
+    const int64_t lds[3] = {p.ldo, p.ldo2, p.ldof};
+    for (int k = 0; k < 3; ++k)
+      if (outs[k] && (!apart(outs[k], es[k], lds[k], p.M, p.N, p.A, sizeof(T), p.lda, p.M, p.K) ||
+                      !apart(outs[k], es[k], lds[k], p.M, p.N, p.B, sizeof(T), p.ldb, rB, cB)))
+        separate = false;
+    if (separate && (int64_t)grid.x * grid.y < 2 * 152) {
+      const dim3 g2 = grid_for(SimtCfgSmall64::BM, SimtCfgSmall64::BN);
+      if (g2.y <= 65535) {
+        if (transB)
+          gemm_simt_kernel<T, true, SimtCfgSmall64><<<g2, 256, 0, s>>>(p);
+        else
+          gemm_simt_kernel<T, false, SimtCfgSmall64><<<g2, 256, 0, s>>>(p);
+        note_launch();
+        return launch_check("gemm_simt");
+      }
+    }
   }
+  if (grid.y > 65535) return KF_ERR_ARG;
   if (transB)
     gemm_simt_kernel<T, true><<<grid, 256, 0, s>>>(p);
   else

@@ -312,6 +312,12 @@ kf_status predict_cov(kf_plan_s* p, const B* src, B* dst) {
 // Covariance part of one filter step t (and the mean update when y != NULL):
 // uses the working P = P_{t|t-1}, writes P_{t|t} to its store slot and
 // leaves P_{t+1|t} in the working P.
+// Block size of the m x m innovation Cholesky (float64): 32-wide leaves and
+// panels.  Its float64 work is bound by the float64 pipe of the SMs it reaches,
+// so smaller blocks (more parallel panel / trailing products, cheaper leaves)
+// finish sooner than the 64-wide blocks used for large float64 matrices.
+constexpr int kSBlock = 32;
+
 template <typename B>
 kf_status filter_step(kf_plan_s* p, int64_t t, const double* y, double* diag_out) {
   cudaStream_t s = p->s;
@@ -334,7 +340,7 @@ kf_status filter_step(kf_plan_s* p, int64_t t, const double* y, double* diag_out
   KF_TRY(innovation_cov<B>(s, m, N, p->H, N, Ut, ldm, p->d.r_kind, p->R, p->S, m, p->partials, kSplitsS));
   const bool joseph = p->d.joseph_every > 0 && (t % p->d.joseph_every) == 0;
   if (joseph) KF_CUDA_TRY(cudaMemcpyAsync(p->S0, p->S, (size_t)m * m * 8, cudaMemcpyDeviceToDevice, s));
-  const int nbS = potrf_block<double>();
+  const int nbS = kSBlock;
   KF_TRY(potrf<double>(s, p->S, m, m, p->Sdinv, nbS, p->status, (int)t));
   const B* L = (const B*)p->S;
   const B* Ld = (const B*)p->Sdinv;
@@ -455,7 +461,7 @@ kf_status filter_step_mixed(kf_plan_s* p, int64_t t, const double* y, double* di
   KF_TRY(innovation_cov<float>(s, m, N, p->H, N, Ut, ldm, p->d.r_kind, p->R, p->S, m, p->partials, kSplitsS));
   const bool joseph = p->d.joseph_every > 0 && (t % p->d.joseph_every) == 0;
   if (joseph) KF_CUDA_TRY(cudaMemcpyAsync(p->S0, p->S, (size_t)m * m * 8, cudaMemcpyDeviceToDevice, s));
-  const int nbS = potrf_block<double>();
+  const int nbS = kSBlock;
   KF_TRY(potrf<double>(s, p->S, m, m, p->Sdinv, nbS, p->status, (int)t));
   KF_TRY((copy2d<float, double>(s, (float*)p->Sl, m, p->S, m, m, m)));
   KF_TRY((copy2d<float, double>(s, (float*)p->Sldinv, nbS, p->Sdinv, nbS, round_up(m, nbS), nbS)));
@@ -556,7 +562,7 @@ kf_status filter_first_fp64(kf_plan_s* p, const double* P0, const double* y, dou
   g.status = p->status;
   KF_TRY(gemm_simt<double>(s, true, g));
   KF_TRY(innovation_cov<double>(s, m, N, p->H, N, p->U64, ldm, p->d.r_kind, p->R, p->S, m, p->partials, kSplitsS));
-  const int nbS = potrf_block<double>();
+  const int nbS = kSBlock;
   KF_TRY(potrf<double>(s, p->S, m, m, p->Sdinv, nbS, p->status, 1));
   KF_TRY((copy2d<double, double>(s, p->Z64, ldm, p->U64, ldm, N, m)));
   KF_TRY(trsm_right<double>(s, true, N, m, p->S, m, p->Sdinv, nbS, p->Z64, ldm, p->status));
