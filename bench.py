@@ -181,7 +181,7 @@ def run_reference(args, world, rank):
               f"oracle); rate = 1 / (filter step + smoother step)")
     per = float(np.mean(times))
     value = 1.0 / per
-    line = {"metric": METRIC, "value": value, "unit": "timesteps/s", "n_gpus": 0, "steps": args.steps,
+    line = {"metric": METRIC, "value": value, "unit": "timesteps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": prob.name.replace("T2", f"T{T_STEPS}"), "N": N_SRC, "m": M_SENS, "T": T_STEPS},
