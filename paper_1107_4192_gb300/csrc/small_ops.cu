@@ -144,15 +144,45 @@ kf_status add_cov(cudaStream_t s, Tdst* dst, int64_t ldd, const Tsrc* src, int64
   return launch_check("add_cov");
 }
 
-// one warp per row, float64 accumulation; each lane reads 4 consecutive
-// elements per step (16-byte loads for aligned float32 rows)
+// One warp per row; each lane reads 4 consecutive elements per step (16-byte
+// loads for aligned rows).  float64 matrices accumulate in float64.  For a
+// float32 matrix (the mixed path's J_t and Z) the products and each lane's
+// running sum are float32 against a float32 copy of x held in shared memory
+// (float64 arithmetic is a small fraction of the float32 rate here), and the
+// 32 lane sums are combined in float64.
+constexpr int kGemvSmemX = 12288;
+
 template <typename T>
-__global__ void gemv_kernel(int64_t rows, int64_t cols, const T* A, int64_t lda, const double* x,
-                            const double* ybase, double sign, double* y) {
+__global__ void __launch_bounds__(256) gemv_kernel(int64_t rows, int64_t cols, const T* A, int64_t lda,
+                                                   const double* x, const double* ybase, double sign, double* y) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const bool vec = aligned_rows(A, lda);
+  if constexpr (sizeof(T) == 4) {
+    __shared__ float xs[kGemvSmemX];
+    if (cols <= kGemvSmemX) {
+      for (int64_t j = threadIdx.x; j < cols; j += blockDim.x) xs[j] = (float)x[j];
+      __syncthreads();
+      for (int64_t i = warp; i < rows; i += nwarps) {
+        const T* row = A + i * lda;
+        float accf = 0.0f;
+#pragma unroll 4
+        for (int64_t j = 4 * lane; j < cols; j += 128) {
+          T a[4];
+          load4<T>(row + j, vec, cols - j, a);
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            if (j + e < cols) accf = fmaf(a[e], xs[j + e], accf);
+        }
+        double acc = accf;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) y[i] = ybase ? ybase[i] + sign * acc : acc;
+      }
+      return;
+    }
+  }
   for (int64_t i = warp; i < rows; i += nwarps) {
     const T* row = A + i * lda;
     double acc = 0.0;
@@ -173,7 +203,9 @@ template <typename T>
 kf_status gemv(cudaStream_t s, int64_t rows, int64_t cols, const T* A, int64_t lda, const double* x,
                const double* ybase, double sign, double* y) {
   if (rows <= 0) return KF_OK;
-  unsigned blocks = (unsigned)std::min<int64_t>(ceil_div(rows * 32, 256), 4096);
+  // float32 rows: 16 rows per block (x is converted once per block)
+  const int64_t per_block_rows = sizeof(T) == 4 ? 16 : 8;
+  unsigned blocks = (unsigned)std::min<int64_t>(ceil_div(rows, per_block_rows), 4096);
   gemv_kernel<T><<<blocks, 256, 0, s>>>(rows, cols, A, lda, x, ybase, sign, y);
   note_launch();
   return launch_check("gemv");
