@@ -212,16 +212,20 @@ __global__ void __launch_bounds__(256, 1) potrf_diag_kernel(T* A, int64_t lda, i
 #pragma unroll
       for (int k = 0; k < 32; ++k) r[k] = S[i * LD + j0 + k];
       int bad = -1;
+      T dnext = T(0);  // warp 0: the next pivot, taken before this column's shared-memory round trip
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
         T* bj = buf + (j & 1) * LA;  // two buffers: a column is written while the previous one may be read
         T q, l;
         if (warp == 0) {
-          const T d = __shfl_sync(0xffffffffu, r[j], j);
+          const T d = j == 0 ? __shfl_sync(0xffffffffu, r[0], 0) : dnext;
           if (bad < 0 && !(d > T(0) && d < T(INFINITY))) bad = j;
           T ljj;
           pivot(d, q, ljj);
           l = lane > j ? r[j] * q : (lane == j ? ljj : T(0));
+          // lane j + 1's diagonal after this column is its entry minus its own l squared,
+          // exactly what the update below computes for it
+          if (j < 31) dnext = __shfl_sync(0xffffffffu, fma(-l, l, r[j + 1]), j + 1);
           bj[lane] = l;
           if (lane == 0) {
             bj[32] = q;
