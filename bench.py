@@ -156,6 +156,53 @@ def cpu_oracle_timestep(prob, T_sample=2):
                      f"(float64 numpy oracle); rate = 1 / (filter step + smoother step)"
 
 
+_CFG0_ORACLE = """
+import sys, time
+import numpy as np
+sys.path.insert(0, {root!r})
+from oracle import kf_oracle as ko
+from paper_1107_4192_gb300 import synth
+p = synth.config0()
+F = np.eye(p.N)
+Q = ko.dense_cov(p.q_kind, p.Q, p.N)
+R = ko.dense_cov(p.r_kind, p.R, p.m)
+P0 = p.p0_scale * np.eye(p.N)
+ts = []
+for _ in range(3):
+    t0 = time.perf_counter()
+    ko.kf_fis(F, Q, p.H, R, p.Y, p.x0, P0)
+    ts.append(time.perf_counter() - t0)
+print(sorted(ts)[1])
+"""
+
+
+def config0_sample(B, solver, synth, torch):
+    """Config 0 (N = 384, m = 64, T = 40) in full: the float64 GPU path through the public API
+    (plan, upload, filter, smoother, download) and the CPU oracle on one core and on all host
+    cores, each the median of 3 runs."""
+    prob = synth.config0()
+    solver.run(prob, prec=B.KF_PREC_FP64)
+    ts = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        solver.run(prob, prec=B.KF_PREC_FP64)
+        torch.cuda.synchronize()
+        ts.append(time.perf_counter() - t0)
+    out = {"workload": "N384_m64_T40 (config 0)", "unit": "timesteps/s",
+           "gpu_fp64_api": prob.T / sorted(ts)[1]}
+    root = os.path.dirname(os.path.abspath(__file__))
+    single = {k: "1" for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS")}
+    for name, extra in (("cpu_oracle_1core", single), ("cpu_oracle_all_cores", {})):
+        env = {k: v for k, v in os.environ.items() if k not in single}
+        env.update(extra)
+        r = subprocess.run([sys.executable, "-c", _CFG0_ORACLE.format(root=root)], capture_output=True, text=True,
+                           env=env, timeout=600)
+        out[name] = prob.T / float(r.stdout.strip().splitlines()[-1]) if r.returncode == 0 else None
+    out["host_cores"] = os.cpu_count()
+    return out
+
+
 def host_threads():
     try:
         import threadpoolctl
@@ -330,6 +377,8 @@ def main():
         line["fp64_plain"] = fp64_plain_prefix(prob, B, solver, synth, torch)
     if rank == 0 and world == 1:
         line["mne_init"] = mne_init_sample(prob, B, solver, torch)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["config0"] = config0_sample(B, solver, synth, torch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         per, sample = cpu_oracle_timestep(synth.config2(T=2))
         line["cpu_baseline"] = {"value": 1.0 / per, "unit": "timesteps/s", "cores": host_threads(), "kind": "oracle",
