@@ -99,45 +99,70 @@ __device__ __forceinline__ void trailing_update(T* S, int LD, int j0, int r0, in
 // One level of the recursive-doubling inverse: for every pair of bs-wide
 // diagonal blocks (A above B), stage 0 forms Tm = L_BA X_AA and stage 1 forms
 // X_BA = -X_BB Tm.  Thread tiles are 4 x 4 with rows and columns strided by
-// bs / 4, so the lanes of a warp read consecutive columns.
+// bs / 4, so the lanes of a warp read consecutive columns.  X_AA and X_BB are
+// lower block-triangular at this point (their upper-right bs/2 quadrant is
+// zero: the diagonal inverses are lower triangular, the blocks above the
+// diagonal were zeroed), so stage 0 skips, for k < bs/2, the columns in the
+// right half (tile columns b >= 2), and stage 1 skips, for k >= bs/2, the rows
+// in the upper half (tile rows a < 2).
+template <typename T, int NB, int bs, int STAGE>
+__device__ __forceinline__ void inverse_stage(const T* S, T* X, T* Tm, int tid) {
+  constexpr int LD = NB + 1, R = bs / 4, NPAIR = NB / (2 * bs), LT = bs + 1, H2 = bs / 2;
+  for (int t = tid; t < NPAIR * R * R; t += 256) {
+    const int q = t / (R * R), ti = (t % (R * R)) / R, tj = t % R;
+    const int a0 = 2 * q * bs, b0 = a0 + bs;
+    const T* Am = STAGE == 0 ? S + b0 * LD + a0 : X + b0 * LD + b0;
+    const T* Bm = STAGE == 0 ? X + a0 * LD + a0 : Tm + q * bs * LT;
+    constexpr int ldb = STAGE == 0 ? LD : LT;
+    T acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+    // k < bs/2: stage 0 has zero B in the right half
+    constexpr int B_LO = STAGE == 0 ? 2 : 4;
+#pragma unroll 4
+    for (int k = 0; k < H2; ++k) {
+      T av[4], bv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) av[a] = Am[(ti + R * a) * LD + k];
+#pragma unroll
+      for (int b = 0; b < B_LO; ++b) bv[b] = Bm[k * ldb + tj + R * b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < B_LO; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+    }
+    // k >= bs/2: stage 1 has zero A in the upper half
+    constexpr int A_HI0 = STAGE == 1 ? 2 : 0;
+#pragma unroll 4
+    for (int k = H2; k < bs; ++k) {
+      T av[4], bv[4];
+#pragma unroll
+      for (int a = A_HI0; a < 4; ++a) av[a] = Am[(ti + R * a) * LD + k];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) bv[b] = Bm[k * ldb + tj + R * b];
+#pragma unroll
+      for (int a = A_HI0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+    }
+    T* out = STAGE == 0 ? Tm + q * bs * LT : X + b0 * LD + a0;
+    constexpr int ldo = STAGE == 0 ? LT : LD;
+    const T sgn = STAGE == 0 ? T(1) : T(-1);
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) out[(ti + R * a) * ldo + tj + R * b] = sgn * acc[a][b];
+  }
+}
+
 template <typename T, int NB, int bs>
 __device__ __forceinline__ void inverse_level(const T* S, T* X, T* Tm, int tid) {
-  constexpr int LD = NB + 1, R = bs / 4, NPAIR = NB / (2 * bs), LT = bs + 1;
-#pragma unroll
-  for (int stage = 0; stage < 2; ++stage) {
-    for (int t = tid; t < NPAIR * R * R; t += 256) {
-      const int q = t / (R * R), ti = (t % (R * R)) / R, tj = t % R;
-      const int a0 = 2 * q * bs, b0 = a0 + bs;
-      const T* Am = stage == 0 ? S + b0 * LD + a0 : X + b0 * LD + b0;
-      const T* Bm = stage == 0 ? X + a0 * LD + a0 : Tm + q * bs * LT;
-      const int ldb = stage == 0 ? LD : LT;
-      T acc[4][4];
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
-#pragma unroll 4
-      for (int k = 0; k < bs; ++k) {
-        T av[4], bv[4];
-#pragma unroll
-        for (int a = 0; a < 4; ++a) av[a] = Am[(ti + R * a) * LD + k];
-#pragma unroll
-        for (int b = 0; b < 4; ++b) bv[b] = Bm[k * ldb + tj + R * b];
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
-      }
-      T* out = stage == 0 ? Tm + q * bs * LT : X + b0 * LD + a0;
-      const int ldo = stage == 0 ? LT : LD;
-      const T sgn = stage == 0 ? T(1) : T(-1);
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) out[(ti + R * a) * ldo + tj + R * b] = sgn * acc[a][b];
-    }
-    __syncthreads();
-  }
+  inverse_stage<T, NB, bs, 0>(S, X, Tm, tid);
+  __syncthreads();
+  inverse_stage<T, NB, bs, 1>(S, X, Tm, tid);
+  __syncthreads();
 }
 
 template <typename T, int NB>

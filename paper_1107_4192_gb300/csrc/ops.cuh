@@ -124,8 +124,8 @@ kf_status innovation(cudaStream_t s, int64_t m, int64_t N, const double* H, cons
 
 // S = H U^T-product + R (m x m, float64), summing float64 partials from
 // split-K chunks of  sum_k H[i, k] Ut[k, j]  (H: m x N float64, Ut: N x m of T).
-template <typename T>
-kf_status innovation_cov(cudaStream_t s, int m, int N, const double* H, int64_t ldh, const T* Ut,
+template <typename T, typename TH>
+kf_status innovation_cov(cudaStream_t s, int m, int N, const TH* H, int64_t ldh, const T* Ut,
                          int64_t ldu, int r_kind, const double* R, double* S, int64_t lds,
                          double* partials, int splits);
 

@@ -337,7 +337,8 @@ kf_status filter_step(kf_plan_s* p, int64_t t, const double* y, double* diag_out
     KF_TRY(gemm_bulk<B>(p, true, g, 3));
   }
   // S = H U^T + R (float64), then its Cholesky factor in place
-  KF_TRY(innovation_cov<B>(s, m, N, p->H, N, Ut, ldm, p->d.r_kind, p->R, p->S, m, p->partials, kSplitsS));
+  KF_TRY((innovation_cov<B, B>(s, m, N, (const B*)p->Hb, p->ldN, Ut, ldm, p->d.r_kind, p->R, p->S, m, p->partials,
+                               kSplitsS)));
   const bool joseph = p->d.joseph_every > 0 && (t % p->d.joseph_every) == 0;
   if (joseph) KF_CUDA_TRY(cudaMemcpyAsync(p->S0, p->S, (size_t)m * m * 8, cudaMemcpyDeviceToDevice, s));
   const int nbS = kSBlock;
@@ -458,7 +459,9 @@ kf_status filter_step_mixed(kf_plan_s* p, int64_t t, const double* y, double* di
     g.status = p->status;
     KF_TRY(tc_gemm_ops(s, p->tc, TcOperand{P, ldN, 1, 0}, TcOperand{p->H, N, 1, 0}, g, 3));
   }
-  KF_TRY(innovation_cov<float>(s, m, N, p->H, N, Ut, ldm, p->d.r_kind, p->R, p->S, m, p->partials, kSplitsS));
+  // H's float copy: the products are float32 either way
+  KF_TRY((innovation_cov<float, float>(s, m, N, (const float*)p->Hb, p->ldN, Ut, ldm, p->d.r_kind, p->R, p->S, m,
+                                      p->partials, kSplitsS)));
   const bool joseph = p->d.joseph_every > 0 && (t % p->d.joseph_every) == 0;
   if (joseph) KF_CUDA_TRY(cudaMemcpyAsync(p->S0, p->S, (size_t)m * m * 8, cudaMemcpyDeviceToDevice, s));
   const int nbS = kSBlock;
@@ -561,7 +564,8 @@ kf_status filter_first_fp64(kf_plan_s* p, const double* P0, const double* y, dou
   g.out = p->U64; g.ldo = ldm;
   g.status = p->status;
   KF_TRY(gemm_simt<double>(s, true, g));
-  KF_TRY(innovation_cov<double>(s, m, N, p->H, N, p->U64, ldm, p->d.r_kind, p->R, p->S, m, p->partials, kSplitsS));
+  KF_TRY((innovation_cov<double, double>(s, m, N, p->H, N, p->U64, ldm, p->d.r_kind, p->R, p->S, m, p->partials,
+                                        kSplitsS)));
   const int nbS = kSBlock;
   KF_TRY(potrf<double>(s, p->S, m, m, p->Sdinv, nbS, p->status, 1));
   KF_TRY((copy2d<double, double>(s, p->Z64, ldm, p->U64, ldm, N, m)));

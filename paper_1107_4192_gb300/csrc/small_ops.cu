@@ -259,8 +259,8 @@ kf_status innovation(cudaStream_t s, int64_t m, int64_t N, const double* H, cons
 
 // partials[split][i][j] = sum_{k in chunk} H[i,k] Ut[k,j]; 32 x 32 output tile per CTA.
 // float32 operands are multiplied in float32 over 32-long runs and summed in float64.
-template <typename T>
-__global__ void __launch_bounds__(256) innov_cov_partial_kernel(int m, int N, const double* H, int64_t ldh,
+template <typename T, typename TH>
+__global__ void __launch_bounds__(256) innov_cov_partial_kernel(int m, int N, const TH* H, int64_t ldh,
                                                                 const T* Ut, int64_t ldu, double* partials,
                                                                 int chunk) {
   __shared__ T Hs[32][33];
@@ -316,14 +316,14 @@ __global__ void innov_cov_reduce_kernel(int m, const double* partials, int split
   }
 }
 
-template <typename T>
-kf_status innovation_cov(cudaStream_t s, int m, int N, const double* H, int64_t ldh, const T* Ut,
+template <typename T, typename TH>
+kf_status innovation_cov(cudaStream_t s, int m, int N, const TH* H, int64_t ldh, const T* Ut,
                          int64_t ldu, int r_kind, const double* R, double* S, int64_t lds,
                          double* partials, int splits) {
   int chunk = (int)round_up(ceil_div(N, splits), 32);
   int used = (int)ceil_div(N, chunk);
   dim3 grid((unsigned)ceil_div(m, 32), (unsigned)ceil_div(m, 32), (unsigned)used);
-  innov_cov_partial_kernel<T><<<grid, 256, 0, s>>>(m, N, H, ldh, Ut, ldu, partials, chunk);
+  innov_cov_partial_kernel<T, TH><<<grid, 256, 0, s>>>(m, N, H, ldh, Ut, ldu, partials, chunk);
   note_launch();
   KF_TRY(launch_check("innov_cov_partial"));
   unsigned blocks = (unsigned)std::min<int64_t>(ceil_div((int64_t)m * m, 256), 1024);
@@ -578,10 +578,12 @@ template kf_status gemv<double>(cudaStream_t, int64_t, int64_t, const double*, i
                                 const double*, double, double*);
 template kf_status gemv<float>(cudaStream_t, int64_t, int64_t, const float*, int64_t, const double*,
                                const double*, double, double*);
-template kf_status innovation_cov<double>(cudaStream_t, int, int, const double*, int64_t, const double*,
-                                          int64_t, int, const double*, double*, int64_t, double*, int);
-template kf_status innovation_cov<float>(cudaStream_t, int, int, const double*, int64_t, const float*,
-                                         int64_t, int, const double*, double*, int64_t, double*, int);
+template kf_status innovation_cov<double, double>(cudaStream_t, int, int, const double*, int64_t, const double*,
+                                                  int64_t, int, const double*, double*, int64_t, double*, int);
+template kf_status innovation_cov<float, double>(cudaStream_t, int, int, const double*, int64_t, const float*,
+                                                 int64_t, int, const double*, double*, int64_t, double*, int);
+template kf_status innovation_cov<float, float>(cudaStream_t, int, int, const float*, int64_t, const float*,
+                                                int64_t, int, const double*, double*, int64_t, double*, int);
 template kf_status diag_extract<double>(cudaStream_t, int64_t, const double*, int64_t, double*);
 template kf_status diag_extract<float>(cudaStream_t, int64_t, const float*, int64_t, double*);
 

@@ -429,12 +429,12 @@ kf_status make_map(CUtensorMap* map, const void* ptr, int64_t rows, int64_t cols
 }
 
 template <int BN, int S, typename TE>
-kf_status launch(cudaStream_t s, const GemmParams<TE>& g, const TcScratch& sc, int64_t ldk) {
+kf_status launch(cudaStream_t s, const GemmParams<TE>& g, const TcScratch& sc, int64_t ldk, bool b_is_a) {
   using C = TcCfg<BN, S>;
   TcMaps maps;
   for (int i = 0; i < S; ++i) {
     KF_TRY(make_map(&maps.a[i], sc.a[i], g.M, ldk, ldk, BM));
-    KF_TRY(make_map(&maps.b[i], sc.b[i], g.N, ldk, ldk, BN));
+    KF_TRY(make_map(&maps.b[i], b_is_a ? sc.a[i] : sc.b[i], g.N, ldk, ldk, BN));
   }
   static std::once_flag configured;
   static cudaError_t cfg_err = cudaSuccess;
@@ -471,9 +471,12 @@ kf_status run_split(cudaStream_t s, TcScratch& sc, const TcOperand& A, const TcO
     oa.planes[i] = sc.a[i];
     ob.planes[i] = sc.b[i];
   }
+  // the same operand on both sides (W^T W): split it once, the B maps read A's planes
+  const bool b_is_a = A.p == B.p && A.ld == B.ld && A.trans == B.trans && A.f64 == B.f64 && g.M == g.N;
+  if (b_is_a) ob.rows = 0;
   KF_TRY(split_bf16_pair(s, oa, ob, slices, ldk));
-  if (slices == 2) return launch<256, 2, TE>(s, g, sc, ldk);
-  return launch<128, 3, TE>(s, g, sc, ldk);
+  if (slices == 2) return launch<256, 2, TE>(s, g, sc, ldk, b_is_a);
+  return launch<128, 3, TE>(s, g, sc, ldk, b_is_a);
 }
 
 }  // namespace
