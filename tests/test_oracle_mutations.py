@@ -50,7 +50,7 @@ def _load_mutant(old, new):
 
 
 def _pins_pass(mod) -> bool:
-    """The subset of pins used to judge a mutant (all hold for the real oracle)."""
+    """The subset of pins used to decide on a mutant (all hold for the real oracle)."""
     prob = synth.random_dense_problem(4, 3, 6, seed=7)
     F, Q, H, R, P0 = oracle_dense(prob)
     try:
