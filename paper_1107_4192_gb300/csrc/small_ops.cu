@@ -123,12 +123,8 @@ __global__ void __launch_bounds__(256) add_cov_kernel(Tdst* dst, int64_t ldd, co
       if (u < units) {
         const int64_t i = u / cpr, j = (u % cpr) * 4;
         Tdst w[4];
-        // Q is zero off the diagonal unless dense: there the sum is the value itself
-        // (float64 arithmetic is a small fraction of float32's on this part, so it is
-        // spent only where Q adds something)
 #pragma unroll
-        for (int e = 0; e < 4; ++e)
-          w[e] = (kind == 2 || i == j + e) ? (Tdst)((double)v[k][e] + cov_value(kind, q, n, i, j + e)) : (Tdst)v[k][e];
+        for (int e = 0; e < 4; ++e) w[e] = (Tdst)((double)v[k][e] + cov_value(kind, q, n, i, j + e));
         store4<Tdst>(dst + i * ldd + j, vd, n - j, w);
       }
     }
@@ -136,12 +132,29 @@ __global__ void __launch_bounds__(256) add_cov_kernel(Tdst* dst, int64_t ldd, co
 }
 
 template <typename Tdst, typename Tsrc>
+__global__ void add_diag_kernel(Tdst* dst, int64_t ldd, const Tsrc* src, int64_t lds, int64_t n, int kind,
+                                const double* q) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i * ldd + i] = (Tdst)((double)src[i * lds + i] + (kind == 0 ? q[0] : q[i]));
+}
+
+template <typename Tdst, typename Tsrc>
 kf_status add_cov(cudaStream_t s, Tdst* dst, int64_t ldd, const Tsrc* src, int64_t lds, int64_t n,
                   int q_kind, const double* q) {
   if (n <= 0) return KF_OK;
-  add_cov_kernel<Tdst, Tsrc><<<sweep_blocks(n * ((n + 3) / 4)), 256, 0, s>>>(dst, ldd, src, lds, n, q_kind, q);
+  if (q_kind == 2 || q_kind < 0) {  // dense Q (or none): every element through float64
+    add_cov_kernel<Tdst, Tsrc><<<sweep_blocks(n * ((n + 3) / 4)), 256, 0, s>>>(dst, ldd, src, lds, n, q_kind, q);
+    note_launch();
+    return launch_check("add_cov");
+  }
+  // scalar or diagonal Q: a plain copy, then the n diagonal sums (kept apart so that the
+  // float64 arithmetic is spent on the diagonal only)
+  if (!((const void*)dst == (const void*)src && ldd == lds && sizeof(Tdst) == sizeof(Tsrc)))
+    KF_TRY((copy2d<Tdst, Tsrc>(s, dst, ldd, src, lds, n, n)));
+  add_diag_kernel<Tdst, Tsrc><<<(unsigned)std::min<int64_t>(ceil_div(n, 256), 1024), 256, 0, s>>>(dst, ldd, src, lds,
+                                                                                                 n, q_kind, q);
   note_launch();
-  return launch_check("add_cov");
+  return launch_check("add_diag");
 }
 
 // One warp per row; each lane reads 4 consecutive elements per step (16-byte
