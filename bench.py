@@ -35,7 +35,8 @@ N_SRC, M_SENS, T_STEPS = 8196, 306, 300
 
 
 def flops_per_timestep(N, m):
-    """Algorithmic flops of one filter step plus one smoother step.
+    """Operation count of one filter step plus one smoother step in the method's standard form
+    (the count the paper's cost discussion and the scope table use; an "equivalent" rate).
 
     filter:   U^T = P H^T (2mN^2), S = H U^T (2m^2N), Cholesky of S (m^3/3),
               K = U^T S^{-1} (2m^2N), P - K U (2mN^2)
@@ -46,6 +47,25 @@ def flops_per_timestep(N, m):
     filt = 4 * m * N * N + 4 * m * m * N + m ** 3 / 3
     smooth = N ** 3 / 3 + 2 * N ** 3 + 2 * N ** 3 + N * N * (N + 1) + 2 * N * N
     return filt + smooth, smooth, filt
+
+
+def executed_flops_per_timestep(N, m, joseph_every, refine_iters=0):
+    """Flops the F = I path with a scalar Q actually executes per time step (each split-bf16
+    product counted once, as one product of its float32 or float64 operands).
+
+    filter:   U^T = P H^T (2mN^2), S = H U^T (2m^2N), Cholesky of S (m^3/3), Z = U^T L^{-T}
+              (m^2N), P - Z Z^T on the lower triangle (mN^2); every k-th step the Joseph form
+              instead: K = Z L^{-1} (m^2N), V = U^T - K S/2 (2m^2N), rank-2m product (2mN^2)
+    smoother: Cholesky of P_{t+1|t} (N^3/3), triangular inverse W = L^{-1} (N^3/3),
+              W^T W with J = I - Q W^T W in its epilogue (N^3/3, lower triangle), W = J D
+              (2N^3), P + W J^T (N^3, lower triangle), mean (2N^2); each refinement iteration
+              of the inverse: residual I - P X (2N^3) and correction X + X R (N^3, symmetric)
+    """
+    filt = 2 * m * N * N + 2 * m * m * N + m ** 3 / 3 + m * m * N + m * N * N
+    if joseph_every:
+        filt += (3 * m * m * N + m * N * N) / joseph_every
+    smooth = N ** 3 + 2 * N ** 3 + N ** 3 + 2 * N * N + refine_iters * 3 * N ** 3
+    return filt + smooth
 
 
 def smoother_gemm_flops_per_launch(N):
@@ -324,14 +344,14 @@ def main():
 
     # Roofline of the smoother's N x N covariance products (W = J D and P + W J^T): in the mixed
     # mode these are the tcgen05 split-bf16 kernel launches timed alone (class 7); otherwise the
-    # phase of the same two products on the CUDA cores.
+    # phase of the same two products on the CUDA cores.  `achieved` counts each product once
+    # (its algorithmic flops); the bf16 operations the tensor cores issue are three per product,
+    # reported separately as the tensor-pipe fraction.
     if args.prec == "mixed" and prof[7][0] > 0:
         n_l, ms_l = prof[7]
         kname = "tc_gemm_kernel<256,2> (split-bf16 W = J D, P + W J^T)"
-        # bf16x3 spends three bf16 products per product: its peak is a third of the measured
-        # sustained bf16 dense peak
-        roof = {"bound": "tensor", "peak": peaks["bf16_tflops_sustained"] / 3, "unit": "TFLOP/s",
-                "peak_note": "bf16_tflops_sustained / 3 (three bf16 products per split-bf16 product)"}
+        roof = {"bound": "tensor", "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s",
+                "peak_note": "bf16_tflops_sustained (measured), the dtype the tensor cores multiply in"}
     else:
         n_l, ms_l = prof[2]
         kname = "gemm_simt (W = J D, P + W J^T)"
@@ -346,7 +366,19 @@ def main():
     traffic = 4.557e9 if args.prec == "mixed" and prof[7][0] > 0 and N == 8196 else None
     roof.update({"kernel": kname, "achieved": achieved, "frac": achieved / roof["peak"], "traffic": traffic,
                  "peak_source": peak_src, "launches": n_l, "avg_launch_ms": avg_s * 1e3,
-                 "work_per_launch": "(2 N^3 + N^2 (N+1)) / 2 flops, N = 8196"})
+                 "work_per_launch": f"(2 N^3 + N^2 (N+1)) / 2 flops, N = {N}"})
+    if roof["bound"] == "tensor":
+        roof["tensor_pipe_frac"] = 3 * achieved / roof["peak"]
+        roof["tensor_pipe_note"] = "three bf16 products issued per split-bf16 product: 3 x achieved / peak"
+    # the smoother-gain solve: Cholesky + triangular inverse of P_{t+1|t} (2 N^3 / 3 per step)
+    # against the same measured bf16 peak (its large products run on the tensor cores)
+    solve_ms = prof[5][1] / max(prof[5][0], 1)
+    roof_solve = {"phase": "solve_factor (Cholesky + inverse of P_{t+1|t})", "bound": "tensor",
+                  "achieved": (2 * N ** 3 / 3) / (solve_ms / 1e3) / 1e12 if solve_ms > 0 else None,
+                  "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s", "peak_source": peak_src,
+                  "ms_per_step": solve_ms, "work_per_step": f"2 N^3 / 3 flops, N = {N}"}
+    if roof_solve["achieved"] is not None:
+        roof_solve["frac"] = roof_solve["achieved"] / roof_solve["peak"]
     names = {0: "filter_update", 1: "innovation", 2: "smoother_gemm", 3: "smoother_solve", 4: "predict",
              5: "solve_factor", 6: "solve_gain", 7: "smoother_gemm_kernel"}
 
@@ -361,8 +393,13 @@ def main():
                        "joseph_every": 16 if args.prec == "mixed" else 0,
                        "parallelism": f"replicas{world}",
                        "l2": "working set > L2 (covariance store of T N x N matrices)"},
-            "tflops": value * total_f / 1e12,
+            "tflops": value * executed_flops_per_timestep(N, m, 16 if args.prec == "mixed" else 0) / 1e12,
+            "tflops_note": "flops the path executes (each split-bf16 product counted once)",
+            "tflops_equivalent": value * total_f / 1e12,
+            "tflops_equivalent_note": "standard operation count of KF + FIS (Cholesky + two N-RHS solves "
+                                      "for the gain), as if the path executed it",
             "roofline": roof,
+            "roofline_solve": roof_solve,
             "gpu_launches": launches,
             "clocks": clocks,
             "e2e": {"value": world * T / e2e_time, "unit": "timesteps/s", "h2d_bytes_per_step": h2d,

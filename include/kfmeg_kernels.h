@@ -26,6 +26,19 @@ kf_status kfx_gemm(int32_t dtype, int32_t transB, int32_t sym, int64_t M, int64_
                    double alpha, const void* A, int64_t lda, const void* B, int64_t ldb,
                    double beta, void* C, int64_t ldc, void* stream);
 
+/* Limit, in nanoseconds of the GPU's global timer, of every pipeline wait
+ * (an mbarrier phase a warp of the tensor-core kernels waits for: operands
+ * landed, accumulator ready, stage free) in kernels launched after this call;
+ * ns = 0 restores the default of 2 s.  A wait that runs out makes the kernel
+ * stop issuing work, wait for what it already issued, free its tensor memory
+ * and raise KF_ERR_TIMEOUT in the calling entry point's status word, which
+ * that entry point returns (its outputs are then undefined).  Limits below
+ * 1 ms poll without suspending the waiting warp.  The setting is process-wide
+ * (all threads and devices).  *previous (if not NULL) receives the old limit.
+ * This is a failure-detection control of the library; the paper has no
+ * counterpart. */
+kf_status kfx_tc_wait_limit(uint64_t ns, uint64_t* previous);
+
 /* Cholesky A = L L^T (lower, in place, n x n; the upper triangle outside the
  * diagonal blocks is untouched), then B <- B A^{-1} = B L^{-T} L^{-1} for the
  * M x n matrix B (skipped when B is NULL).  This is the solve of the smoother

@@ -249,16 +249,3 @@ def scalar_riccati_fixed_point(q: float, h: float, r: float):
     """
     a = 0.5 * (q + np.sqrt(q * q + 4.0 * q * r / (h * h)))
     return a, a - q
-
-
-# --------------------------------------------------------------- helpers
-
-def problem_arrays(N, m, f_kind, F_csr, q_kind, Q, r_kind, R, P0):
-    """Dense F, Q, R, P0 for the oracle from the interface's input forms."""
-    if f_kind == 0:
-        F = np.eye(N)
-    elif f_kind == 1:
-        F = dense_from_csr(N, *F_csr)
-    else:
-        F = np.array(F_csr, dtype=np.float64, copy=True)
-    return F, dense_cov(q_kind, Q, N), dense_cov(r_kind, R, m), np.asarray(P0, float)

@@ -64,6 +64,7 @@ _SIGS = {
     "kf_plan_destroy": (None, [_P]),
     "kf_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "kfx_gemm": (ctypes.c_int, [_I32, _I32, _I32, _I64, _I64, _I64, _D, _P, _I64, _P, _I64, _D, _P, _I64, _P]),
+    "kfx_tc_wait_limit": (ctypes.c_int, [ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)]),
     "kfx_posv_right": (ctypes.c_int, [_I32, _I64, _P, _I64, _I64, _P, _I64, ctypes.POINTER(_I64), _P]),
     "kfx_posv_right_static": (ctypes.c_int, [_I32, _I64, _P, _I64, _I64, _P, _I64, ctypes.POINTER(_I64), _P]),
     "kfx_spmm_fpft": (ctypes.c_int, [_I32, _I64, _P, _P, _P, _P, _I64, _P, _I64, _I32, _P, _P]),
@@ -223,6 +224,13 @@ def kf_plan_launch_count(plan) -> int:
 def kfx_gemm(dtype, transB, sym, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, stream=None):
     _check(lib().kfx_gemm(dtype, transB, sym, M, N, K, alpha, _ptr(A), lda, _ptr(B), ldb, beta, _ptr(C), ldc,
                           _stream(stream)), "kfx_gemm")
+
+
+def kfx_tc_wait_limit(ns: int) -> int:
+    """Sets the tensor-core kernels' pipeline-wait limit (0 = default 2 s); returns the old one."""
+    prev = ctypes.c_uint64()
+    _check(lib().kfx_tc_wait_limit(ns, ctypes.byref(prev)), "kfx_tc_wait_limit")
+    return prev.value
 
 
 def kfx_posv_right(dtype, n, A, lda, M, B, ldb, stream=None):

@@ -57,19 +57,33 @@ kf_status kfx_gemm(int32_t dtype, int32_t transB, int32_t sym, int64_t M, int64_
     std::vector<void*> mem;
     int64_t rows = M > N ? M : N;
     int64_t ld = round_up(K > 0 ? K : 1, 64);
-    st = tc_scratch_alloc(sc, rows, ld, [&](void** ptr, size_t bytes) -> kf_status {
+    auto alloc = [&](void** ptr, size_t bytes) -> kf_status {
       if (cudaMalloc(ptr, bytes) != cudaSuccess) return KF_ERR_CUDA;
       mem.push_back(*ptr);
       return KF_OK;
-    });
+    };
+    int* status = nullptr;
+    st = alloc((void**)&status, ST_WORDS * sizeof(int));
+    if (st == KF_OK && cudaMemsetAsync(status, 0, ST_WORDS * sizeof(int), s) != cudaSuccess) st = KF_ERR_CUDA;
+    if (st == KF_OK) st = tc_scratch_alloc(sc, rows, ld, alloc);
+    g.status = status;
     if (st == KF_OK) st = tc_gemm_split(s, sc, g, dtype == 2 ? 2 : 3, transB != 0);
+    int h[ST_WORDS] = {0, 0, 0, 0};
+    if (status) cudaMemcpyAsync(h, status, sizeof(h), cudaMemcpyDeviceToHost, s);
     cudaStreamSynchronize(s);
     for (void* p : mem) cudaFree(p);
+    if (st == KF_OK && h[ST_CODE]) st = (kf_status)h[ST_CODE];
   } else {
     return KF_ERR_ARG;
   }
   if (st != KF_OK) return st;
   KF_CUDA_TRY(cudaStreamSynchronize(s));
+  return KF_OK;
+}
+
+kf_status kfx_tc_wait_limit(uint64_t ns, uint64_t* previous) {
+  const uint64_t prev = g_tc_wait_ns.exchange(ns == 0 ? kTcDefaultWaitNs : ns);
+  if (previous) *previous = prev;
   return KF_OK;
 }
 

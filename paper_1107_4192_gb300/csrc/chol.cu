@@ -360,12 +360,7 @@ template <typename T, int NB>
 static kf_status launch_potrf_diag(cudaStream_t s, T* A, int64_t lda, int n, T* dinv, int64_t ldd, int* status,
                                    int step, int base) {
   const size_t smem = DiagSmem<T, NB>::bytes;
-  static std::once_flag configured;
-  static cudaError_t cfg_err = cudaSuccess;
-  std::call_once(configured, [&] {
-    cfg_err = cudaFuncSetAttribute(potrf_diag_kernel<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  });
-  KF_CUDA_TRY(cfg_err);
+  KF_CUDA_TRY(smem_limit_per_device((const void*)potrf_diag_kernel<T, NB>, (int)smem));
   potrf_diag_kernel<T, NB><<<1, 256, smem, s>>>(A, lda, n, dinv, ldd, status, step, base);
   note_launch();
   return launch_check("potrf_diag");

@@ -8,6 +8,9 @@
 
 #include <algorithm>
 #include <atomic>
+#include <mutex>
+#include <set>
+#include <utility>
 
 #include "../../include/kfmeg.h"
 
@@ -77,6 +80,22 @@ extern thread_local int64_t t_launches;
 inline void note_launch(int64_t n = 1) {
   g_launches += n;
   t_launches += n;
+}
+
+// Raises the dynamic shared-memory limit of kernel `fn` to `bytes` on the
+// current device.  The attribute belongs to one device, so it is set once per
+// (kernel, device) pair: a process that uses several GPUs configures each.
+inline cudaError_t smem_limit_per_device(const void* fn, int bytes) {
+  static std::mutex mu;
+  static std::set<std::pair<const void*, int>> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done.count({fn, dev})) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) done.insert({fn, dev});
+  return e;
 }
 
 }  // namespace kfm

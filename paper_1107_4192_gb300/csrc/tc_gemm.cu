@@ -24,9 +24,11 @@
 //           registers after every k-tile, and at the end stage the tile in
 //           shared memory and apply the covariance epilogue in coalesced row
 //           and (for mirrored symmetric outputs) column sweeps.
-// Every mbarrier wait is bounded (about 2 s of %globaltimer); on expiry the
-// kernel raises KF_ERR_TIMEOUT in the status word, stops issuing, waits
-// (bounded) for what it already issued, frees TMEM and returns.
+// Every mbarrier wait is bounded by %globaltimer: the pipeline waits by a
+// limit passed as a kernel argument (2 s unless kfx_tc_wait_limit set another),
+// the clean-up waits by their own 2 s.  On expiry the kernel raises
+// KF_ERR_TIMEOUT in the status word, stops issuing, waits (bounded) for what
+// it already issued, frees TMEM and returns.
 #include <cuda.h>
 
 #include <mutex>
@@ -42,7 +44,7 @@ constexpr int BM = 128;
 constexpr int BK = 64;          // one 128-byte swizzle atom of bf16
 constexpr int UMMA_K = 16;
 constexpr int NUM_THREADS = 320;  // TMA warp, MMA warp, 8 epilogue warps
-constexpr uint64_t WAIT_NS = 2000000000ull;
+constexpr uint64_t WAIT_NS = 2000000000ull;  // clean-up waits, and the default pipeline limit
 
 template <int BN, int S>  // S = bf16 slices per operand: 2 -> 3 products, 3 -> 6 products
 struct TcCfg {
@@ -86,8 +88,30 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait on an mbarrier phase; false on timeout or when another role aborted.
-__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+__device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase; false on timeout or when another role
+// aborted.  Limits of 1 ms and more use the suspending try_wait and read the
+// clock every 64 polls; shorter limits poll without suspending and read the
+// clock after every poll, so the limit alone decides when the wait ends.
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, uint64_t limit_ns = WAIT_NS) {
+  if (limit_ns < 1000000ull) {
+    const uint64_t t0 = globaltimer();
+    for (;;) {
+      if (mbar_test_wait(bar, parity)) return true;
+      if (*abort_flag || globaltimer() - t0 > limit_ns) return false;
+    }
+  }
   uint64_t t0 = 0;
   for (uint32_t it = 0;; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
@@ -96,7 +120,7 @@ __device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_fla
       const uint64_t now = globaltimer();
       if (t0 == 0)
         t0 = now;
-      else if (now - t0 > WAIT_NS)
+      else if (now - t0 > limit_ns)
         return false;
     }
   }
@@ -163,7 +187,7 @@ constexpr int KC = 1;  // k-tiles accumulated in TMEM before promotion to regist
 // by one thread per column half.
 template <int BN, int S, typename TE>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
-    tc_gemm_kernel(const __grid_constant__ TcMaps maps, const GemmParams<TE> p, int num_k_tiles) {
+    tc_gemm_kernel(const __grid_constant__ TcMaps maps, const GemmParams<TE> p, int num_k_tiles, uint64_t wait_ns) {
   using C = TcCfg<BN, S>;
   constexpr int HALF = BN / 2;
   extern __shared__ uint8_t smem_raw[];
@@ -229,7 +253,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       const int kt = kt0 + it;
       const int s = it % C::STAGES;
       const uint32_t ph = (uint32_t)(it / C::STAGES) & 1u;
-      if (!mbar_wait(empty_bar(s), ph ^ 1u, abort_flag)) {
+      if (!mbar_wait(empty_bar(s), ph ^ 1u, abort_flag, wait_ns)) {
         *abort_flag = 1;
         status_set(p.status, KF_ERR_TIMEOUT, p.step, 1);
         break;
@@ -251,14 +275,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     // ---------------- MMA issuer: chunk c accumulates into TMEM buffer c & 1
     for (int it = 0; it < nk; ++it) {
       const int c = it / KC, buf = c & 1;
-      if (it % KC == 0 && !mbar_wait(acce_bar(buf), ((uint32_t)(c >> 1) & 1u) ^ 1u, abort_flag)) {
+      if (it % KC == 0 && !mbar_wait(acce_bar(buf), ((uint32_t)(c >> 1) & 1u) ^ 1u, abort_flag, wait_ns)) {
         *abort_flag = 1;
         status_set(p.status, KF_ERR_TIMEOUT, p.step, 4);
         break;
       }
       const int s = it % C::STAGES;
       const uint32_t ph = (uint32_t)(it / C::STAGES) & 1u;
-      if (!mbar_wait(full_bar(s), ph, abort_flag)) {
+      if (!mbar_wait(full_bar(s), ph, abort_flag, wait_ns)) {
         *abort_flag = 1;
         status_set(p.status, KF_ERR_TIMEOUT, p.step, 2);
         break;
@@ -296,7 +320,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     bool ok = true;
     for (int c = 0; c < nchunks && ok; ++c) {
       const int buf = c & 1;
-      if (!mbar_wait(accf_bar(buf), (uint32_t)(c >> 1) & 1u, abort_flag)) {
+      if (!mbar_wait(accf_bar(buf), (uint32_t)(c >> 1) & 1u, abort_flag, wait_ns)) {
         if (!*abort_flag) {
           *abort_flag = 1;
           status_set(p.status, KF_ERR_TIMEOUT, p.step, 3);
@@ -436,16 +460,11 @@ kf_status launch(cudaStream_t s, const GemmParams<TE>& g, const TcScratch& sc, i
     KF_TRY(make_map(&maps.a[i], sc.a[i], g.M, ldk, ldk, BM));
     KF_TRY(make_map(&maps.b[i], b_is_a ? sc.a[i] : sc.b[i], g.N, ldk, ldk, BN));
   }
-  static std::once_flag configured;
-  static cudaError_t cfg_err = cudaSuccess;
-  std::call_once(configured, [&] {
-    cfg_err = cudaFuncSetAttribute(tc_gemm_kernel<BN, S, TE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
-  });
-  KF_CUDA_TRY(cfg_err);
+  KF_CUDA_TRY(smem_limit_per_device((const void*)tc_gemm_kernel<BN, S, TE>, (int)C::SMEM));
   dim3 grid((unsigned)ceil_div(g.N, BN), (unsigned)ceil_div(g.M, BM));
   const int num_k_tiles = (int)(ldk / BK);
   if (g_tc_timer) g_tc_timer->before(s);
-  tc_gemm_kernel<BN, S, TE><<<grid, NUM_THREADS, C::SMEM, s>>>(maps, g, num_k_tiles);
+  tc_gemm_kernel<BN, S, TE><<<grid, NUM_THREADS, C::SMEM, s>>>(maps, g, num_k_tiles, g_tc_wait_ns.load());
   if (g_tc_timer) g_tc_timer->after(s);
   note_launch();
   return launch_check("tc_gemm");
@@ -482,6 +501,7 @@ kf_status run_split(cudaStream_t s, TcScratch& sc, const TcOperand& A, const TcO
 }  // namespace
 
 thread_local TcLaunchTimer* g_tc_timer = nullptr;
+std::atomic<uint64_t> g_tc_wait_ns{WAIT_NS};
 
 uint64_t tc_scratch_bytes(int64_t rows, int64_t ld) { return 6ull * rows * ld * sizeof(__nv_bfloat16); }
 

@@ -27,6 +27,11 @@ struct TcLaunchTimer {
 };
 extern thread_local TcLaunchTimer* g_tc_timer;
 
+// Limit (ns of %globaltimer) of the tensor-core kernels' pipeline waits,
+// passed to each launch; the default is 2 s.
+extern std::atomic<uint64_t> g_tc_wait_ns;
+constexpr uint64_t kTcDefaultWaitNs = 2000000000ull;
+
 // True when this build carries the tcgen05 kernels.
 bool tc_available();
 

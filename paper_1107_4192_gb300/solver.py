@@ -30,11 +30,14 @@ class DeviceInputs:
     P0: object
 
 
-def host_inputs(prob):
-    """numpy arrays in the layout of the C interface (row-major, float64/int64)."""
+def host_inputs(prob, dense_F=False):
+    """numpy arrays in the layout of the C interface (row-major, float64/int64).
+    dense_F: pass F as a dense N x N matrix (KF_F_DENSE) instead of compressed rows."""
     f64 = lambda a: np.ascontiguousarray(np.asarray(a, dtype=np.float64))
-    if prob.F is None:
+    if prob.F is None and not dense_F:
         f_kind, F, rp, col, nnz = B.KF_F_IDENTITY, None, None, None, 0
+    elif dense_F:
+        f_kind, F, rp, col, nnz = B.KF_F_DENSE, f64(prob.F_dense()), None, None, 0
     else:
         f_kind, nnz = B.KF_F_CSR, prob.F.nnz
         F, rp, col = f64(prob.F.val), np.ascontiguousarray(prob.F.rowptr, np.int64), \
@@ -46,9 +49,9 @@ def host_inputs(prob):
                 r_kind=prob.r_kind, R=R, Y=f64(prob.Y), x0=f64(prob.x0), P0=P0)
 
 
-def upload(prob, device="cuda") -> DeviceInputs:
+def upload(prob, device="cuda", dense_F=False) -> DeviceInputs:
     import torch
-    h = host_inputs(prob)
+    h = host_inputs(prob, dense_F)
     t = lambda a: None if a is None else torch.from_numpy(a).to(device)
     if prob.P0 is None:  # build the scaled identity on the device
         P0 = torch.eye(prob.N, dtype=torch.float64, device=device) * float(prob.p0_scale)
@@ -109,9 +112,9 @@ class Plan:
 
 
 def run(prob, prec=B.KF_PREC_FP64, solve_prec=B.KF_SOLVE_FP64, joseph_every=0, checkpoint_every=0,
-        t_full=-1, split_terms=0, device="cuda"):
+        t_full=-1, split_terms=0, device="cuda", dense_F=False):
     """Filter + smoother for a synthetic problem; returns numpy outputs."""
-    d = upload(prob, device)
+    d = upload(prob, device, dense_F)
     with Plan.for_inputs(d, prob.N, prob.m, prob.T, prec=prec, solve_prec=solve_prec, joseph_every=joseph_every,
                          checkpoint_every=checkpoint_every, split_terms=split_terms) as plan:
         xf, df = plan.filter(d)

@@ -309,6 +309,27 @@ def random_dense_problem(N: int, m: int, T: int, seed: int, name: str = "") -> P
     return prob
 
 
+def dense_dynamics_problem(N: int, m: int, T: int, seed: int, name: str = "") -> Problem:
+    """Fully dense, non-symmetric F = 0.85 I + 0.05 G / sqrt(N) (G Gaussian, spectral radius
+    below 1), dense Q, R and P0, non-zero x0: the general linear model of eqn 3.  F is kept in
+    compressed-row form with every entry present, so it can be passed either way."""
+    rng = np.random.default_rng(seed)
+    Fd = 0.85 * np.eye(N) + 0.05 * rng.standard_normal((N, N)) / np.sqrt(N)
+    Fm = CSR(N, np.arange(0, N * N + 1, N, dtype=np.int64), np.tile(np.arange(N, dtype=np.int64), N),
+             Fd.reshape(-1).copy())
+    Aq = rng.standard_normal((N, N)) / np.sqrt(N)
+    Qd = 0.02 * np.eye(N) + 0.01 * Aq @ Aq.T
+    Ar = rng.standard_normal((m, m)) / np.sqrt(m)
+    Rd = 0.5 * np.eye(m) + 0.2 * Ar @ Ar.T
+    Ap = rng.standard_normal((N, N)) / np.sqrt(N)
+    P0 = 0.5 * np.eye(N) + 0.3 * Ap @ Ap.T
+    H = lead_field(rng, m, N)
+    x0 = rng.standard_normal(N)
+    _, Y = simulate_state_space(rng, N, m, T, Fd, Qd, Rd, x0, P0, H)
+    return Problem(N, m, T, H, Y, x0, 1.0, 2, Qd, 2, Rd, F=Fm, P0=P0,
+                   name=name or f"densedyn_N{N}_m{m}_T{T}", seed=seed)
+
+
 # ------------------------------------------------------- named workloads
 
 def config0() -> Problem:

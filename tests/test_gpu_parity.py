@@ -103,6 +103,62 @@ def test_checkpoint_recompute_is_bitwise_identical(prec):
             assert np.array_equal(full[k], part[k]), (c, k)
 
 
+@pytest.mark.parametrize("mesh", [False, True])
+@pytest.mark.parametrize("c", [2, 5])
+def test_mixed_checkpoint_recompute(mesh, c):
+    """Mixed path with only every c-th P_{t|t} kept: the skipped steps are recomputed during the
+    smoother from float32 checkpoints (the float64 working covariance restarts from a float32
+    value), so results differ from the full store by rounding only; both stay within the mixed
+    tolerances of the oracle."""
+    prob = synth.mesh_problem(324, 30, 17, seed=8, identity_F=not mesh)
+    kw = dict(prec=B.KF_PREC_MIXED_BF16X3, solve_prec=B.KF_SOLVE_FP32, joseph_every=4)
+    ref = run_oracle(prob)
+    full = solver.run(prob, **kw)
+    part = solver.run(prob, checkpoint_every=c, **kw)
+    check(part, ref, TOL_MEAN32, TOL_DIAG32)
+    # the filter pass is the same launch sequence either way
+    assert np.array_equal(full["x_filt"], part["x_filt"])
+    assert rel_err_per_step(part["x_smooth"], full["x_smooth"]) <= 1e-5
+
+
+@pytest.mark.parametrize("prec,solve,tm,td", [
+    (B.KF_PREC_FP64, B.KF_SOLVE_FP64, TOL64, TOL64),
+    (B.KF_PREC_FP32, B.KF_SOLVE_FP64, TOL_MEAN32, TOL_DIAG32),
+    (B.KF_PREC_MIXED_BF16X3, B.KF_SOLVE_FP32, TOL_MEAN32, TOL_DIAG32),
+    (B.KF_PREC_MIXED_BF16X3, B.KF_SOLVE_FP64, TOL_MEAN32, TOL_DIAG32)])
+@pytest.mark.parametrize("N,m,T", [(200, 20, 8), (257, 70, 5)])
+def test_dense_F(prec, solve, tm, td, N, m, T):
+    """General dense, non-symmetric F passed as a dense N x N matrix (KF_F_DENSE), dense Q, R, P0."""
+    prob = synth.dense_dynamics_problem(N, m, T, seed=N + T)
+    out = solver.run(prob, prec=prec, solve_prec=solve, joseph_every=3, dense_F=True)
+    check(out, run_oracle(prob), tm, td)
+
+
+def test_dense_F_equals_compressed_rows_fp64():
+    """The same F given densely and as compressed rows with every entry present: same result to
+    float64 rounding."""
+    prob = synth.dense_dynamics_problem(150, 13, 6, seed=2)
+    a = solver.run(prob, prec=B.KF_PREC_FP64, dense_F=True)
+    b = solver.run(prob, prec=B.KF_PREC_FP64)
+    for k in a:
+        assert rel_err_per_step(a[k], b[k]) <= 1e-12, k
+
+
+def test_mixed_long_epoch_T300():
+    """Mixed path over a 300-step epoch (Joseph form every 16 steps, float32 store), the
+    configuration of the N = 8196 benchmark at N = 1024: the split-bf16 error must not build up
+    through the smoother's covariance recursion beyond the mixed tolerances."""
+    prob = synth.mesh_problem(1024, 306, 300, seed=11, identity_F=True)
+    ref = run_oracle(prob)
+    out = solver.run(prob, prec=B.KF_PREC_MIXED_BF16X3, solve_prec=B.KF_SOLVE_FP32, joseph_every=16)
+    errs = dict(x_filt=rel_err_per_step(out["x_filt"], ref["x_filt"]),
+                x_smooth=rel_err_per_step(out["x_smooth"], ref["x_smooth"]),
+                diagP_filt=rel_err_elementwise(out["diagP_filt"], diag_of(ref["P_filt"])),
+                diagP_smooth=rel_err_elementwise(out["diagP_smooth"], diag_of(ref["P_smooth"])))
+    print("mixed N=1024 m=306 T=300 errors vs oracle:", errs)
+    check(out, ref, TOL_MEAN32, TOL_DIAG32)
+
+
 def test_full_smoothed_covariance_output():
     prob = synth.random_dense_problem(90, 11, 6, seed=12)
     ref = run_oracle(prob)

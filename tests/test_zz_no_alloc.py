@@ -72,3 +72,20 @@ def test_static_rejects_sizes_above_the_limit():
     dA = torch.zeros(1, dtype=torch.float64, device="cuda")
     st, fi = B.kfx_posv_right_static(0, n, dA, n, 0, None, n)
     assert st == B.KF_ERR_ARG and fi == -1
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+@pytest.mark.parametrize("n", [4096, 4000])
+def test_static_at_the_size_limit(dtype, n):
+    """n = 4096 fills the fixed scratch exactly (the diagonal-block inverses of both dtypes come to
+    the whole array); 4000 leaves a ragged last block.  Small M keeps the solve cheap."""
+    rng = np.random.default_rng(n + dtype)
+    G = rng.standard_normal((n, n))
+    A = G @ G.T / n + np.eye(n)
+    Bm = rng.standard_normal((3, n))
+    st0, fi0, L0, X0 = _solve(B.kfx_posv_right, dtype, A, Bm)
+    st1, fi1, L1, X1 = _solve(B.kfx_posv_right_static, dtype, A, Bm)
+    assert st0 == st1 == 0 and fi0 == fi1 == -1
+    tl, tx = TOL[dtype]
+    assert np.abs(L1 - L0).max() <= tl * np.abs(L0).max()
+    assert np.linalg.norm(X1 - X0) <= tx * np.linalg.norm(X0)
