@@ -26,6 +26,39 @@ kf_status kfx_gemm(int32_t dtype, int32_t transB, int32_t sym, int64_t M, int64_
                    double alpha, const void* A, int64_t lda, const void* B, int64_t ldb,
                    double beta, void* C, int64_t ldc, void* stream);
 
+/* C = alpha A B^T + beta C + delta I to float64 accuracy on the tensor cores:
+ * the exact-slice product (Ozaki et al. 2012; exponent-aligned integer slices
+ * as in Mukunoki et al. 2020) that forms the float64 residuals of the
+ * smoother-gain solve (eqn 11; see kfx_spd_inverse).  Row i of A and row j of
+ * B are cut into `levels` slices of 8 bits below their largest magnitude; the
+ * slice products whose levels sum to less than `levels` are accumulated
+ * exactly and summed in 64-bit integers, so element (i, j) is within about
+ * 2^(5 - 8 levels) K max|A[i,:]| max|B[j,:]| of the exact product (2^-51 for
+ * levels = 7, float64 class; 2^-35 for levels = 5).
+ *   A: M x K, B: N x K (row-major, leading dimensions lda, ldb), float64, or
+ *      float32 when a_f32 / b_f32 is set.  C: M x N float64 (in/out when
+ *      beta != 0).  K <= 2^20.  levels: 5 or 7.
+ * Allocates its slice buffers (about 2 levels (M + N) K bytes) for the call.
+ * Returns KF_ERR_ARG on bad sizes, KF_ERR_UNSUPPORTED without tcgen05. */
+kf_status kfx_gemm_exact(int32_t levels, int64_t M, int64_t N, int64_t K, double alpha, const void* A, int64_t lda,
+                         int32_t a_f32, const void* B, int64_t ldb, int32_t b_f32, double beta, double delta, double* C,
+                         int64_t ldc, void* stream);
+
+/* X = A^{-1} for a symmetric positive definite float32 A (n x n, lower
+ * triangle read), float64 X (n x n, full), on the tensor cores: the inverse
+ * the smoother gain of eqn 11 needs (J_t = P_{t|t} F^T P_{t+1|t}^{-1}).
+ *   mode 1: float32-class: recursive Cholesky A = L L^T, W = L^{-1} (split-bf16
+ *           products, float32 diagonal blocks), X = W^T W;
+ *   mode 2: float64-accurate: mode 1's X refined by two Newton steps
+ *           X <- X + X (I - A X) whose residuals I - A X are exact-slice
+ *           products (kfx_gemm_exact with 5, then 7 levels): the result
+ *           agrees with a float64 inversion to float64 rounding times the
+ *           condition number.
+ * A non-positive pivot returns KF_ERR_NOT_PD with *fail_index (else -1).
+ * Allocates its work buffers for the call. */
+kf_status kfx_spd_inverse(int32_t mode, int64_t n, const float* A, int64_t lda, double* X, int64_t ldx,
+                          int64_t* fail_index, void* stream);
+
 /* Limit, in nanoseconds of the GPU's global timer, of every pipeline wait
  * (an mbarrier phase a warp of the tensor-core kernels waits for: operands
  * landed, accumulator ready, stage free) in kernels launched after this call;

@@ -64,6 +64,9 @@ _SIGS = {
     "kf_plan_destroy": (None, [_P]),
     "kf_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "kfx_gemm": (ctypes.c_int, [_I32, _I32, _I32, _I64, _I64, _I64, _D, _P, _I64, _P, _I64, _D, _P, _I64, _P]),
+    "kfx_gemm_exact": (ctypes.c_int, [_I32, _I64, _I64, _I64, _D, _P, _I64, _I32, _P, _I64, _I32, _D, _D, _P, _I64,
+                                      _P]),
+    "kfx_spd_inverse": (ctypes.c_int, [_I32, _I64, _P, _I64, _P, _I64, ctypes.POINTER(_I64), _P]),
     "kfx_tc_wait_limit": (ctypes.c_int, [ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)]),
     "kfx_posv_right": (ctypes.c_int, [_I32, _I64, _P, _I64, _I64, _P, _I64, ctypes.POINTER(_I64), _P]),
     "kfx_posv_right_static": (ctypes.c_int, [_I32, _I64, _P, _I64, _I64, _P, _I64, ctypes.POINTER(_I64), _P]),
@@ -224,6 +227,22 @@ def kf_plan_launch_count(plan) -> int:
 def kfx_gemm(dtype, transB, sym, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, stream=None):
     _check(lib().kfx_gemm(dtype, transB, sym, M, N, K, alpha, _ptr(A), lda, _ptr(B), ldb, beta, _ptr(C), ldc,
                           _stream(stream)), "kfx_gemm")
+
+
+def kfx_gemm_exact(levels, M, N, K, alpha, A, lda, B, ldb, beta, delta, C, ldc, stream=None):
+    """C = alpha A B^T + beta C + delta I as an exact-slice tensor-core product (float64 C)."""
+    import torch
+    a32 = 1 if A.dtype == torch.float32 else 0
+    b32 = 1 if B.dtype == torch.float32 else 0
+    _check(lib().kfx_gemm_exact(levels, M, N, K, alpha, _ptr(A), lda, a32, _ptr(B), ldb, b32, beta, delta, _f64(C),
+                                ldc, _stream(stream)), "kfx_gemm_exact")
+
+
+def kfx_spd_inverse(mode, n, A, lda, X, ldx, stream=None):
+    """X = A^{-1} (float32 SPD A, float64 X); mode 1 float32-class, 2 float64-accurate."""
+    fi = _I64()
+    st = lib().kfx_spd_inverse(mode, n, _ptr(A), lda, _f64(X), ldx, ctypes.byref(fi), _stream(stream))
+    return st, fi.value
 
 
 def kfx_tc_wait_limit(ns: int) -> int:

@@ -3,6 +3,8 @@
 
 #include "../../include/kfmeg_kernels.h"
 #include "ops.cuh"
+#include "ozaki.cuh"
+#include "solve_tc.cuh"
 #include "tc_gemm.cuh"
 
 using namespace kfm;
@@ -79,6 +81,108 @@ kf_status kfx_gemm(int32_t dtype, int32_t transB, int32_t sym, int64_t M, int64_
   if (st != KF_OK) return st;
   KF_CUDA_TRY(cudaStreamSynchronize(s));
   return KF_OK;
+}
+
+kf_status kfx_gemm_exact(int32_t levels, int64_t M, int64_t N, int64_t K, double alpha, const void* A, int64_t lda,
+                         int32_t a_f32, const void* B, int64_t ldb, int32_t b_f32, double beta, double delta, double* C,
+                         int64_t ldc, void* stream) {
+  if (M < 1 || N < 1 || K < 1 || M > INT32_MAX || N > INT32_MAX || K > (1 << 20)) return KF_ERR_ARG;
+  if (!A || !B || !C || lda < K || ldb < K || ldc < N || (levels != 5 && levels != 7)) return KF_ERR_ARG;
+  if (!tc_available()) return KF_ERR_UNSUPPORTED;
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<void*> mem;
+  auto alloc = [&](void** ptr, size_t bytes) -> kf_status {
+    if (cudaMalloc(ptr, bytes) != cudaSuccess) return KF_ERR_CUDA;
+    mem.push_back(*ptr);
+    return KF_OK;
+  };
+  OzSlices sa, sb;
+  void *ma = nullptr, *mb = nullptr;
+  int* status = nullptr;
+  kf_status st = alloc(&ma, oz_slice_bytes(M, K, levels));
+  if (st == KF_OK) st = alloc(&mb, oz_slice_bytes(N, K, levels));
+  if (st == KF_OK) st = alloc((void**)&status, ST_WORDS * sizeof(int));
+  if (st == KF_OK && cudaMemsetAsync(status, 0, ST_WORDS * sizeof(int), s) != cudaSuccess) st = KF_ERR_CUDA;
+  if (st == KF_OK) {
+    oz_slice_layout(sa, ma, M, K, levels);
+    oz_slice_layout(sb, mb, N, K, levels);
+    st = oz_slice(s, A, lda, a_f32 ? 0 : 1, M, K, levels, sa);
+  }
+  if (st == KF_OK) st = oz_slice(s, B, ldb, b_f32 ? 0 : 1, N, K, levels, sb);
+  if (st == KF_OK) {
+    OzEpilogue e;
+    e.alpha = alpha;
+    e.delta = delta;
+    if (beta != 0.0) {
+      e.cin = C;
+      e.ldcin = ldc;
+      e.beta = beta;
+    }
+    e.out = C;
+    e.ldo = ldc;
+    e.status = status;
+    st = oz_gemm(s, sa, sb, (int)M, (int)N, (int)K, levels, e);
+  }
+  int h[ST_WORDS] = {0, 0, 0, 0};
+  if (status) cudaMemcpyAsync(h, status, sizeof(h), cudaMemcpyDeviceToHost, s);
+  cudaError_t ce = cudaStreamSynchronize(s);
+  for (void* p : mem) cudaFree(p);
+  if (st != KF_OK) return st;
+  if (ce != cudaSuccess) return KF_ERR_CUDA;
+  return (kf_status)h[ST_CODE];
+}
+
+kf_status kfx_spd_inverse(int32_t mode, int64_t n, const float* A, int64_t lda, double* X, int64_t ldx,
+                          int64_t* fail_index, void* stream) {
+  if (fail_index) *fail_index = -1;
+  if (n < 1 || n > (1 << 16) || !A || !X || lda < n || ldx < n || (mode != 1 && mode != 2)) return KF_ERR_ARG;
+  if (!tc_available()) return KF_ERR_UNSUPPORTED;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t ld = round_up(n, 128);
+  std::vector<void*> mem;
+  auto alloc = [&](void** ptr, size_t bytes) -> kf_status {
+    if (cudaMalloc(ptr, bytes) != cudaSuccess) return KF_ERR_CUDA;
+    mem.push_back(*ptr);
+    return KF_OK;
+  };
+  float *L = nullptr, *W = nullptr, *T = nullptr;
+  void* rmem = nullptr;
+  int* status = nullptr;
+  TcScratch sc;
+  kf_status st = alloc((void**)&L, n * ld * 4);
+  if (st == KF_OK) st = alloc((void**)&W, n * ld * 4);
+  if (st == KF_OK) st = alloc((void**)&T, n * ld * 4);
+  if (st == KF_OK) st = alloc((void**)&status, ST_WORDS * sizeof(int));
+  if (st == KF_OK && mode == 2) st = alloc(&rmem, refine_bytes(n, ld));
+  if (st == KF_OK) st = tc_scratch_alloc(sc, n, ld, alloc);
+  if (st == KF_OK && (cudaMemsetAsync(status, 0, ST_WORDS * sizeof(int), s) != cudaSuccess ||
+                      cudaMemsetAsync(W, 0, n * ld * 4, s) != cudaSuccess))
+    st = KF_ERR_CUDA;
+  if (st == KF_OK) st = copy2d<float, float>(s, L, ld, A, lda, n, n, true);
+  if (st == KF_OK) st = chol_inverse_tc(s, sc, (int)n, L, ld, W, ld, T, ld, status, 1);
+  if (st == KF_OK && mode == 1) {
+    GemmParams<double> g;  // X = W^T W
+    g.M = (int)n; g.N = (int)n; g.K = (int)n;
+    g.out = X; g.ldo = ldx;
+    g.sym = 1;
+    g.tri_a = -1;
+    g.tri_b = -1;
+    g.status = status;
+    st = tc_gemm_ops(s, sc, TcOperand{W, ld, 0, 1}, TcOperand{W, ld, 0, 1}, g, 3);
+  } else if (st == KF_OK) {
+    RefineBufs rb;
+    refine_layout(rb, rmem, n, ld);
+    st = refine_inverse_tc(s, sc, (int)n, A, lda, W, ld, rb, 0, nullptr, nullptr, nullptr, 0,
+                           X, ldx, status, 1);
+  }
+  int h[ST_WORDS] = {0, 0, 0, 0};
+  if (status) cudaMemcpyAsync(h, status, sizeof(h), cudaMemcpyDeviceToHost, s);
+  cudaError_t ce = cudaStreamSynchronize(s);
+  for (void* p : mem) cudaFree(p);
+  if (st != KF_OK) return st;
+  if (ce != cudaSuccess) return KF_ERR_CUDA;
+  if (h[ST_CODE] && fail_index) *fail_index = h[ST_INDEX];
+  return (kf_status)h[ST_CODE];
 }
 
 kf_status kfx_tc_wait_limit(uint64_t ns, uint64_t* previous) {

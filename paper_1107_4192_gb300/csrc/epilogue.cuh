@@ -26,6 +26,10 @@ __device__ __forceinline__ void epilogue_store(const GemmParams<T>& p, int gi, i
     const T d = gi == gj ? T(1) : T(0);
     p.out[(int64_t)gi * p.ldo + gj] = d - qi * vpre;
     if (mirror) p.out[(int64_t)gj * p.ldo + gi] = d - qj * vpre;
+    if (p.outf) {
+      p.outf[(int64_t)gi * p.ldof + gj] = (float)(d - qi * vpre);
+      if (mirror) p.outf[(int64_t)gj * p.ldof + gi] = (float)(d - qj * vpre);
+    }
     return;
   }
   if (p.out) {
@@ -61,7 +65,9 @@ __device__ __forceinline__ T epilogue_row(const GemmParams<T>& p, int gi, int gj
   if (p.cin) vpre += p.beta * cin_v;
   if (p.gain_q) {
     const T qi = (T)(p.gain_q_kind == 0 ? p.gain_q[0] : p.gain_q[gi]);
-    p.out[(int64_t)gi * p.ldo + gj] = (gi == gj ? T(1) : T(0)) - qi * vpre;
+    const T jv = (gi == gj ? T(1) : T(0)) - qi * vpre;
+    p.out[(int64_t)gi * p.ldo + gj] = jv;
+    if (p.outf) p.outf[(int64_t)gi * p.ldof + gj] = (float)jv;
     return vpre;
   }
   T v = vpre;
@@ -84,6 +90,7 @@ __device__ __forceinline__ void epilogue_mirror(const GemmParams<T>& p, int gi, 
   if (p.gain_q) {
     const T qi = (T)(p.gain_q_kind == 0 ? p.gain_q[0] : p.gain_q[gi]);
     p.out[(int64_t)gi * p.ldo + gj] = -qi * v;  // off-diagonal: delta = 0
+    if (p.outf) p.outf[(int64_t)gi * p.ldof + gj] = (float)(-qi * v);
     return;
   }
   if (p.out) p.out[(int64_t)gi * p.ldo + gj] = v;

@@ -52,7 +52,8 @@ struct GemmParams {
   int tri_a = 0, tri_b = 0;
   // Smoother gain from an inverse (J = I - Q P^{-1}, F = I): when gain_q is
   // set, out receives delta_ij - q_i (alpha acc + beta cin) with q_i = gain_q[0]
-  // (gain_q_kind 0) or gain_q[i] (1); a mirrored element uses q_j.
+  // (gain_q_kind 0) or gain_q[i] (1); a mirrored element uses q_j; outf (if
+  // set) a float32 copy.
   const double* gain_q = nullptr;
   int gain_q_kind = -1;
 };

@@ -1,0 +1,369 @@
+// Exact-slice (Ozaki-scheme) products on the 5th-generation tensor cores.
+//
+// Slicing (oz_slice_kernel): one CTA per row finds the row's largest
+// magnitude, takes its binary exponent e (max < 2^e) and writes the integer
+// slices q_p = rint(v_p), v_0 = x 2^(7-e), v_{p+1} = 256 (v_p - q_p), all exact
+// in float64, as bf16 planes.
+//
+// Product (oz_gemm_kernel): one 128 x 64 output tile per CTA, 18 warps.
+//   warp 0  one lane issues the TMA loads (64-byte swizzle) of all slices of a
+//           32-wide k-slice of A and B into a shared-memory stage;
+//   warp 1  allocates TMEM (one 128 x 64 float32 accumulator per slice level),
+//           one lane issues, per stage and level, the MMAs of the level's
+//           slice pairs into that level's accumulator, and after the last
+//           k-slice of a 128-wide chunk commits each level to its "ready"
+//           barrier; a level's first MMA of the next chunk waits until the
+//           epilogue has drained it;
+//   warps 2-17 per chunk and level, read the accumulator (an exact integer
+//           below 2^24), convert it to an integer and add it into 64-bit
+//           fixed-point accumulators in registers (levels 0-2 and levels 3..
+//           in two of them); at the end scale by the row and column exponents
+//           and apply the float64 epilogue.
+// The drain of level l overlaps the MMAs of the later levels.  Every
+// pipeline wait is bounded (kernel argument, as in the split-bf16 kernel).
+#include "ozaki.cuh"
+#include "tc_ptx.cuh"
+
+namespace kfm {
+
+namespace {
+
+constexpr int OZ_BM = 128;      // output rows per CTA (TMEM lanes)
+constexpr int OZ_BN = 64;       // output columns per CTA (TMEM columns per level)
+constexpr int OZ_BK = 32;       // k per stage: one 64-byte swizzle row of bf16
+constexpr int OZ_CK = 4;        // k-slices per exact chunk (128 values of k)
+constexpr int OZ_EPI_WARPS = 16;  // 4 TMEM lane quadrants x 4 column quarters of 16
+constexpr int OZ_THREADS = 32 * (2 + OZ_EPI_WARPS);
+constexpr int OZ_GROUP = 8;     // row tiles per rasterisation group (operand reuse in L2)
+constexpr int OZ_ROW_PAD = 128;
+
+template <int LV>
+struct OzCfg {
+  static constexpr int A_BYTES = OZ_BM * OZ_BK * 2;
+  static constexpr int B_BYTES = OZ_BN * OZ_BK * 2;
+  static constexpr int STAGE_BYTES = LV * (A_BYTES + B_BYTES);
+  static constexpr int FIT = (200 * 1024) / STAGE_BYTES;
+  static constexpr int STAGES = FIT > 4 ? 4 : FIT;
+  static_assert(STAGES >= 2, "double-buffered pipeline");
+  static_assert(LV * OZ_BN <= 512, "one TMEM accumulator per level");
+  // a level has at most LV slice pairs whose products are below 2^14 in magnitude, so one
+  // chunk of OZ_CK * OZ_BK values of k sums to an integer below 2^24: exact in float32
+  static_assert(LV * OZ_CK * OZ_BK * 16384 <= (1 << 24), "exact chunk");
+  static_assert(2 * STAGES + 2 * LV + 1 <= 28, "barriers fit their 256 bytes");
+  static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
+  // instruction descriptor: D = f32, A = B = bf16, both K-major, N >> 3, M >> 4
+  static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_BN >> 3) << 17) |
+                                    ((uint32_t)(OZ_BM >> 4) << 24);
+};
+
+struct OzMaps {
+  CUtensorMap a, b;  // all slice planes of A (box 32 x 128) and of B (box 32 x 64)
+};
+
+struct OzArgs {
+  int M, N, nk;                  // nk = k-slices of OZ_BK
+  int a_rows_pad, b_rows_pad;    // plane p starts at row p * rows_pad of its map
+  const int* ea;
+  const int* eb;
+  OzEpilogue e;
+  uint64_t wait_ns;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) oz_slice_kernel(const T* X, int64_t ld, int64_t rows, int64_t cols, int S,
+                                                       __nv_bfloat16* planes, int64_t rows_pad, int64_t ldk,
+                                                       int* exps) {
+  __shared__ double red[8];
+  const int64_t r = blockIdx.x;
+  const T* row = X + r * ld;
+  double mx = 0.0;
+  if (r < rows)
+    for (int64_t k = threadIdx.x; k < cols; k += blockDim.x) mx = fmax(mx, fabs((double)row[k]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = mx;
+  __syncthreads();
+  mx = red[0];
+  for (int w = 1; w < (int)blockDim.x / 32; ++w) mx = fmax(mx, red[w]);
+  int e = 0;
+  if (mx > 0.0 && isfinite(mx)) frexp(mx, &e);  // mx = f 2^e, 0.5 <= f < 1
+  if (threadIdx.x == 0) exps[r] = e;
+  const int64_t pstride = rows_pad * ldk;
+  for (int64_t k0 = threadIdx.x * 8; k0 < ldk; k0 += (int64_t)blockDim.x * 8) {
+    double v[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = (r < rows && k0 + i < cols) ? scalbn((double)row[k0 + i], 7 - e) : 0.0;
+    for (int p = 0; p < S; ++p) {
+      uint32_t w[4];
+#pragma unroll
+      for (int i = 0; i < 8; i += 2) {
+        const double q0 = rint(v[i]), q1 = rint(v[i + 1]);  // |q| <= 128: exact in bf16
+        w[i / 2] = (uint32_t)__bfloat16_as_ushort(__double2bfloat16(q0)) |
+                   ((uint32_t)__bfloat16_as_ushort(__double2bfloat16(q1)) << 16);
+        v[i] = (v[i] - q0) * 256.0;
+        v[i + 1] = (v[i + 1] - q1) * 256.0;
+      }
+      *reinterpret_cast<uint4*>(planes + p * pstride + r * ldk + k0) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  }
+}
+
+template <int LV>
+__global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_constant__ OzMaps maps, const OzArgs a) {
+  using C = OzCfg<LV>;
+  extern __shared__ uint8_t smem_raw[];
+  // grouped rasterisation: OZ_GROUP row tiles sweep the column tiles together
+  const int tiles_m = (a.M + OZ_BM - 1) / OZ_BM, tiles_n = (a.N + OZ_BN - 1) / OZ_BN;
+  const int per_group = OZ_GROUP * tiles_n;
+  const int t = blockIdx.x, grp = t / per_group, first_m = grp * OZ_GROUP;
+  const int gsize = min(tiles_m - first_m, OZ_GROUP);
+  const int local = t - grp * per_group;
+  const int m0 = (first_m + local % gsize) * OZ_BM, n0 = (local / gsize) * OZ_BN;
+
+  const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  uint8_t* gbase = smem_raw + (base - smem_u32(smem_raw));
+  const uint32_t bars = base + C::STAGES * C::STAGE_BYTES;
+  auto full_bar = [&](int s) { return bars + 8u * s; };
+  auto empty_bar = [&](int s) { return bars + 8u * (C::STAGES + s); };
+  auto ready_bar = [&](int l) { return bars + 8u * (2 * C::STAGES + l); };
+  auto drained_bar = [&](int l) { return bars + 8u * (2 * C::STAGES + LV + l); };
+  const uint32_t done_bar = bars + 8u * (2 * C::STAGES + 2 * LV);
+  uint32_t* tmem_slot =
+      reinterpret_cast<uint32_t*>(gbase + C::STAGES * C::STAGE_BYTES + 8 * (2 * C::STAGES + 2 * LV + 1));
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  volatile int* skip_flag = reinterpret_cast<volatile int*>(tmem_slot + 2);
+  volatile int never = 0;  // abort flag of the clean-up waits, which must not stop early
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < C::STAGES; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    for (int l = 0; l < LV; ++l) {
+      mbar_init(ready_bar(l), 1);
+      mbar_init(drained_bar(l), OZ_EPI_WARPS);
+    }
+    mbar_init(done_bar, 1);
+    *abort_flag = 0;
+    *skip_flag = status_failed(a.e.status) ? 1 : 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_slot))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  const bool skip = *skip_flag != 0;
+  const int nk = a.nk;
+  const int nchunks = (nk + OZ_CK - 1) / OZ_CK;
+  bool mma_issued = false;
+
+  if (skip) {
+    // an earlier kernel failed: do nothing but release TMEM below
+  } else if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer
+    int last_round[4] = {-1, -1, -1, -1};
+    for (int it = 0; it < nk; ++it) {
+      const int s = it % C::STAGES;
+      const uint32_t ph = (uint32_t)(it / C::STAGES) & 1u;
+      if (!mbar_wait(empty_bar(s), ph ^ 1u, abort_flag, a.wait_ns)) {
+        *abort_flag = 1;
+        status_set(a.e.status, KF_ERR_TIMEOUT, a.e.step, 11);
+        break;
+      }
+      const uint32_t st = base + s * C::STAGE_BYTES;
+      mbar_expect_tx(full_bar(s), C::STAGE_BYTES);
+      const int x = it * OZ_BK;
+#pragma unroll
+      for (int p = 0; p < LV; ++p) tma_load_2d(st + p * C::A_BYTES, &maps.a, x, p * a.a_rows_pad + m0, full_bar(s));
+#pragma unroll
+      for (int p = 0; p < LV; ++p)
+        tma_load_2d(st + LV * C::A_BYTES + p * C::B_BYTES, &maps.b, x, p * a.b_rows_pad + n0, full_bar(s));
+      last_round[s] = it / C::STAGES;
+    }
+    if (*abort_flag) {  // let issued copies land before the CTA's shared memory goes away
+      for (int s = 0; s < C::STAGES; ++s)
+        if (last_round[s] >= 0) mbar_wait(full_bar(s), (uint32_t)last_round[s] & 1u, &never);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer: level l accumulates into TMEM columns [64 l, 64 l + 64)
+    bool ok = true;
+    for (int it = 0; it < nk && ok; ++it) {
+      const int s = it % C::STAGES;
+      const uint32_t ph = (uint32_t)(it / C::STAGES) & 1u;
+      if (!mbar_wait(full_bar(s), ph, abort_flag, a.wait_ns)) {
+        *abort_flag = 1;
+        status_set(a.e.status, KF_ERR_TIMEOUT, a.e.step, 12);
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t st = base + s * C::STAGE_BYTES;
+      const int c = it / OZ_CK;
+      const bool first = (it % OZ_CK) == 0;
+      const bool last = (it % OZ_CK) == OZ_CK - 1 || it == nk - 1;
+#pragma unroll
+      for (int l = 0; l < LV; ++l) {
+        if (first && c > 0 && !mbar_wait(drained_bar(l), (uint32_t)(c - 1) & 1u, abort_flag, a.wait_ns)) {
+          *abort_flag = 1;
+          status_set(a.e.status, KF_ERR_TIMEOUT, a.e.step, 13);
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t dacc = tmem + (uint32_t)(l * OZ_BN);
+#pragma unroll
+        for (int pa = 0; pa <= l; ++pa) {
+          const int pb = l - pa;
+#pragma unroll
+          for (int kk = 0; kk < OZ_BK / 16; ++kk) {
+            const uint32_t acc = (first && pa == 0 && kk == 0) ? 0u : 1u;
+            mma_bf16(dacc, smem_desc_sw(st + pa * C::A_BYTES + kk * 32, 512, kLayoutSw64),
+                     smem_desc_sw(st + LV * C::A_BYTES + pb * C::B_BYTES + kk * 32, 512, kLayoutSw64), C::IDESC,
+                     acc);
+          }
+        }
+        mma_issued = true;
+        if (last) mma_commit(ready_bar(l));
+      }
+      if (ok) mma_commit(empty_bar(s));
+    }
+  } else if (warp >= 2) {
+    // ---------------- epilogue: exact level sums into 64-bit fixed point, then scale and store
+    const int q = warp % 4, h = (warp - 2) / 4;  // TMEM lane quadrant (fixed by the warp index), column quarter
+    const int gi = m0 + 32 * q + lane;
+    long long hi[16], lo[16];  // levels 0-2 in units of level 2; levels 3.. in units of level LV-1
+#pragma unroll
+    for (int j = 0; j < 16; ++j) hi[j] = lo[j] = 0;
+    bool ok = true;
+    for (int c = 0; c < nchunks && ok; ++c) {
+#pragma unroll
+      for (int l = 0; l < LV; ++l) {
+        if (!mbar_wait(ready_bar(l), (uint32_t)c & 1u, abort_flag, a.wait_ns)) {
+          if (!*abort_flag) {
+            *abort_flag = 1;
+            status_set(a.e.status, KF_ERR_TIMEOUT, a.e.step, 14);
+          }
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        uint32_t r[16];
+        tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(l * OZ_BN + h * 16), r);
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(drained_bar(l)) : "memory");
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const long long v = (long long)__float2int_rn(__uint_as_float(r[j]));
+          if (l < 3)
+            hi[j] += v << (8 * (2 - l));
+          else
+            lo[j] += v << (8 * (LV - 1 - l));
+        }
+      }
+    }
+    if (ok && !*abort_flag && gi < a.M) {
+      const int ei = a.ea[gi];
+      const OzEpilogue& e = a.e;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int gj = n0 + h * 16 + j;
+        if (gj < a.N) {
+          const int sc = ei + a.eb[gj] - 14;
+          const double cval = scalbn((double)hi[j], sc - 16) + scalbn((double)lo[j], sc - 8 * (LV - 1));
+          double v = e.alpha * cval;
+          if (e.cin) v += e.beta * e.cin[(int64_t)gi * e.ldcin + gj];
+          if (gi == gj) v += e.delta;
+          e.out[(int64_t)gi * e.ldo + gj] = v;
+          if (e.outf) e.outf[(int64_t)gi * e.ldof + gj] = (float)v;
+        }
+      }
+    }
+  }
+  // every issued MMA must have finished before TMEM is freed
+  if (!skip && warp == 1 && lane == 0 && mma_issued) {
+    mma_commit(done_bar);
+    mbar_wait(done_bar, 0, &never);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+  }
+}
+
+template <int LV>
+kf_status launch_oz(cudaStream_t s, const OzSlices& A, const OzSlices& B, int M, int N, int K, const OzEpilogue& e) {
+  using C = OzCfg<LV>;
+  OzMaps maps;
+  KF_TRY(tma_map_bf16(&maps.a, A.planes, (int64_t)A.S * A.rows_pad, A.ldk, A.ldk, OZ_BK, OZ_BM, 64));
+  KF_TRY(tma_map_bf16(&maps.b, B.planes, (int64_t)B.S * B.rows_pad, B.ldk, B.ldk, OZ_BK, OZ_BN, 64));
+  OzArgs a;
+  a.M = M;
+  a.N = N;
+  a.nk = (int)ceil_div(K, OZ_BK);
+  a.a_rows_pad = (int)A.rows_pad;
+  a.b_rows_pad = (int)B.rows_pad;
+  a.ea = A.exps;
+  a.eb = B.exps;
+  a.e = e;
+  a.wait_ns = g_tc_wait_ns.load();
+  KF_CUDA_TRY(smem_limit_per_device((const void*)oz_gemm_kernel<LV>, (int)C::SMEM));
+  const int64_t tiles = ceil_div(M, OZ_BM) * ceil_div(N, OZ_BN);
+  if (g_tc_timer) g_tc_timer->before(s);
+  oz_gemm_kernel<LV><<<(unsigned)tiles, OZ_THREADS, C::SMEM, s>>>(maps, a);
+  if (g_tc_timer) g_tc_timer->after(s);
+  note_launch();
+  return launch_check("oz_gemm");
+}
+
+}  // namespace
+
+uint64_t oz_slice_bytes(int64_t rows, int64_t cols, int S) {
+  const uint64_t rp = round_up(std::max<int64_t>(rows, 1), OZ_ROW_PAD), ldk = round_up(std::max<int64_t>(cols, 1), 64);
+  return round_up((int64_t)(S * rp * ldk * 2), 256) + rp * 4;
+}
+
+void oz_slice_layout(OzSlices& out, void* mem, int64_t rows, int64_t cols, int S) {
+  out.rows = rows;
+  out.rows_pad = round_up(std::max<int64_t>(rows, 1), OZ_ROW_PAD);
+  out.ldk = round_up(std::max<int64_t>(cols, 1), 64);
+  out.S = S;
+  out.planes = static_cast<__nv_bfloat16*>(mem);
+  out.exps = reinterpret_cast<int*>(static_cast<char*>(mem) + round_up((int64_t)(S * out.rows_pad * out.ldk * 2), 256));
+}
+
+kf_status oz_slice(cudaStream_t s, const void* X, int64_t ld, int f64, int64_t rows, int64_t cols, int S,
+                   OzSlices& out) {
+  if (rows < 1 || cols < 1 || S < 1 || S > out.S || rows > out.rows_pad || cols > out.ldk || ld < cols || !X)
+    return KF_ERR_ARG;
+  out.rows = rows;
+  out.filled = S;
+  if (f64)
+    oz_slice_kernel<double><<<(unsigned)out.rows_pad, 256, 0, s>>>(static_cast<const double*>(X), ld, rows, cols, S,
+                                                                   out.planes, out.rows_pad, out.ldk, out.exps);
+  else
+    oz_slice_kernel<float><<<(unsigned)out.rows_pad, 256, 0, s>>>(static_cast<const float*>(X), ld, rows, cols, S,
+                                                                  out.planes, out.rows_pad, out.ldk, out.exps);
+  note_launch();
+  return launch_check("oz_slice");
+}
+
+kf_status oz_gemm(cudaStream_t s, const OzSlices& A, const OzSlices& B, int M, int N, int K, int levels,
+                  const OzEpilogue& e) {
+  if (M <= 0 || N <= 0) return KF_OK;
+  if (K < 1 || K > (1 << 20) || !e.out) return KF_ERR_ARG;
+  if (M > A.rows || N > B.rows || K > A.ldk || K > B.ldk) return KF_ERR_ARG;
+  if (A.filled < levels || B.filled < levels) return KF_ERR_ARG;
+  if (levels == 5) return launch_oz<5>(s, A, B, M, N, K, e);
+  if (levels == 7) return launch_oz<7>(s, A, B, M, N, K, e);
+  return KF_ERR_ARG;
+}
+
+}  // namespace kfm

@@ -1,0 +1,68 @@
+// Exact-slice products on the tensor cores: float64-accurate C = A B^T from
+// bf16 tcgen05 MMAs (the splitting scheme of Ozaki et al. 2012, "Error-free
+// transformations of matrix multiplication by using fast routines of matrix
+// multiplication and its applications", with the exponent-aligned integer
+// slices of Mukunoki, Ozaki, Ogita and Imamura 2020, "DGEMM using Tensor Cores,
+// and Its Accurate and Reproducible Versions").
+//
+// Row r of an operand X (rows x K) is written as
+//     X[r][k] = 2^(e_r - 7) * sum_{p < S} 2^(-8p) q_p[r][k]
+// with e_r the exponent of the row's largest magnitude (max |X[r][:]| < 2^e_r)
+// and integer slices q_p in [-128, 128], each exact in bf16.  A product of two
+// slices is an integer below 2^14, so the sum over k of the products of one
+// slice level l = p_A + p_B is an exact integer as long as it stays below 2^24:
+// the tensor cores' float32 accumulation (which truncates) then loses nothing.
+// The products with l < L are kept (L(L+1)/2 slice pairs); the dropped levels
+// and the slices' own truncation leave an error in element (i, j) of about
+// 2^(-8L+3) K 2^(e_i + e_j) (per term, 2^(-8L+3) of the row maxima's product):
+// 2^-37 for L = 5, 2^-53 for L = 7.
+#pragma once
+
+#include "tc_gemm.cuh"
+
+namespace kfm {
+
+// Slices of a rows x cols operand: S planes of rows_pad x ldk bf16 (plane p at
+// planes + p * rows_pad * ldk; rows >= rows and columns >= cols are zero) and
+// the per-row exponents e_r (rows_pad ints, 0 for zero rows).
+struct OzSlices {
+  __nv_bfloat16* planes = nullptr;
+  int* exps = nullptr;
+  int64_t rows = 0, rows_pad = 0, ldk = 0;
+  int S = 0;       // planes the memory holds
+  int filled = 0;  // planes the last oz_slice wrote
+};
+
+// Bytes of the planes and exponents for rows x cols with S slices.
+uint64_t oz_slice_bytes(int64_t rows, int64_t cols, int S);
+// Points `out` at memory of oz_slice_bytes(rows, cols, S) bytes.
+void oz_slice_layout(OzSlices& out, void* mem, int64_t rows, int64_t cols, int S);
+
+// Fills `out` (laid out by oz_slice_layout for at least these rows, cols and
+// S slices) from X (float64 when f64, else float32; rows x cols, leading
+// dimension ld, row-major).  A non-finite row gives NaN slices.
+kf_status oz_slice(cudaStream_t s, const void* X, int64_t ld, int f64, int64_t rows, int64_t cols, int S,
+                   OzSlices& out);
+
+// Epilogue of the exact-slice product, float64:
+//   out[i][j] = alpha * (A B^T)[i][j] + beta * cin[i][j] + (i == j ? delta : 0)
+// (cin optional); outf (optional) receives a float32 copy.
+struct OzEpilogue {
+  double alpha = 1.0, beta = 0.0, delta = 0.0;
+  const double* cin = nullptr;
+  int64_t ldcin = 0;
+  double* out = nullptr;
+  int64_t ldo = 0;
+  float* outf = nullptr;
+  int64_t ldof = 0;
+  int* status = nullptr;  // KF_ERR_TIMEOUT on an expired wait; kernels skip when already failed
+  int step = 0;
+};
+
+// C = A B^T for A (M x K) and B (N x K) given by their slices, keeping the
+// slice levels l < levels (5 or 7; both operands need at least `levels`
+// slices).  K <= 2^20.
+kf_status oz_gemm(cudaStream_t s, const OzSlices& A, const OzSlices& B, int M, int N, int K, int levels,
+                  const OzEpilogue& e);
+
+}  // namespace kfm

@@ -176,4 +176,73 @@ kf_status gain_identity_tc(cudaStream_t s, TcScratch& sc, int n, const float* W,
   return tc_gemm_ops(s, sc, TcOperand{W, ldw, 0, 1}, TcOperand{W, ldw, 0, 1}, g, 3);
 }
 
+uint64_t refine_bytes(int64_t n, int64_t ld) {
+  const uint64_t mat = round_up((int64_t)(n * ld * 8), 256);
+  return 3 * mat + 2 * round_up((int64_t)oz_slice_bytes(n, n, 7), 256);
+}
+
+void refine_layout(RefineBufs& rb, void* mem, int64_t n, int64_t ld) {
+  const uint64_t mat = round_up((int64_t)(n * ld * 8), 256);
+  char* p = static_cast<char*>(mem);
+  rb.X0 = reinterpret_cast<double*>(p);
+  rb.R = reinterpret_cast<double*>(p + mat);
+  rb.X1 = reinterpret_cast<double*>(p + 2 * mat);
+  rb.ld = ld;
+  oz_slice_layout(rb.Ps, p + 3 * mat, n, n, 7);
+  oz_slice_layout(rb.Xs, p + 3 * mat + round_up((int64_t)oz_slice_bytes(n, n, 7), 256), n, n, 7);
+}
+
+kf_status refine_inverse_tc(cudaStream_t s, TcScratch& sc, int n, const float* P, int64_t ldp, const float* W,
+                            int64_t ldw, RefineBufs& rb, int q_kind, const double* gain_q, double* J64, float* Jf,
+                            int64_t ldj, double* X2, int64_t ldx, int* status, int step) {
+  if (gain_q && q_kind != 0 && q_kind != 1) return KF_ERR_ARG;
+  const int64_t ld = rb.ld;
+  {
+    GemmParams<double> g;  // X0 = W^T W (lower triangle + mirror; row r of W^T is zero for k < r)
+    g.M = n; g.N = n; g.K = n;
+    g.out = rb.X0; g.ldo = ld;
+    g.sym = 1;
+    g.tri_a = -1;
+    g.tri_b = -1;
+    g.status = status;
+    KF_TRY(tc_gemm_ops(s, sc, TcOperand{W, ldw, 0, 1}, TcOperand{W, ldw, 0, 1}, g, 3));
+  }
+  KF_TRY(oz_slice(s, P, ldp, 0, n, n, 7, rb.Ps));
+  const double* X = rb.X0;
+  for (int k = 0; k < 2; ++k) {
+    // R_k = I - P X_k  (X_k symmetric: its rows are the product's columns)
+    KF_TRY(oz_slice(s, X, ld, 1, n, n, k == 0 ? 5 : 7, rb.Xs));
+    OzEpilogue e;
+    e.alpha = -1.0;
+    e.delta = 1.0;
+    e.out = rb.R;
+    e.ldo = ld;
+    e.status = status;
+    e.step = step;
+    KF_TRY(oz_gemm(s, rb.Ps, rb.Xs, n, n, n, k == 0 ? 5 : 7, e));
+    // X_{k+1} = X_k + X_k R_k;  C = op(A) op(B)^T with op(B) = R_k^T (R_k stored K x N)
+    GemmParams<double> g;
+    g.M = n; g.N = n; g.K = n;
+    g.cin = X; g.ldcin = ld; g.beta = 1.0;
+    g.sym = 1;
+    g.status = status;
+    g.step = step;
+    if (k == 0) {
+      g.out = rb.X1; g.ldo = ld;
+      KF_TRY(tc_gemm_ops(s, sc, TcOperand{X, ld, 1, 0}, TcOperand{rb.R, ld, 1, 1}, g, 3));
+      X = rb.X1;
+    } else if (gain_q) {
+      // the correction is ~1e-9 of X: two bf16 slices (16 bits) leave it accurate to ~1e-14 of X
+      g.gain_q = gain_q; g.gain_q_kind = q_kind;
+      g.out = J64; g.ldo = ldj;
+      g.outf = Jf; g.ldof = ldj;
+      KF_TRY(tc_gemm_ops(s, sc, TcOperand{X, ld, 1, 0}, TcOperand{rb.R, ld, 1, 1}, g, 2));
+    } else {
+      g.out = X2; g.ldo = ldx;
+      KF_TRY(tc_gemm_ops(s, sc, TcOperand{X, ld, 1, 0}, TcOperand{rb.R, ld, 1, 1}, g, 2));
+    }
+  }
+  return KF_OK;
+}
+
 }  // namespace kfm

@@ -1,6 +1,7 @@
 // Tensor-core smoother-gain solve (mixed mode with float32 solve).
 #pragma once
 
+#include "ozaki.cuh"
 #include "tc_gemm.cuh"
 
 namespace kfm {
@@ -22,5 +23,30 @@ kf_status gain_from_inverse_tc(cudaStream_t s, TcScratch& sc, int n, const float
 // epilogue, so P_{t+1|t}^{-1} itself is never stored.
 kf_status gain_identity_tc(cudaStream_t s, TcScratch& sc, int n, const float* W, int64_t ldw, int q_kind,
                            const double* q, float* J, int64_t ldj, int* status);
+
+// Buffers of refine_inverse_tc: three n x ld float64 matrices and the slices
+// of P (7 slices) and of the iterate (7 slices).
+struct RefineBufs {
+  double *X0 = nullptr, *R = nullptr, *X1 = nullptr;
+  int64_t ld = 0;
+  OzSlices Ps, Xs;
+};
+uint64_t refine_bytes(int64_t n, int64_t ld);
+void refine_layout(RefineBufs& rb, void* mem, int64_t n, int64_t ld);
+
+// Inverse of the symmetric positive definite P (float32, n x n) to float64
+// accuracy, from W = L^{-1} of its float32-class factor (chol_inverse_tc):
+//   X0 = W^T W;   R_k = I - P X_k;   X_{k+1} = X_k + X_k R_k   (k = 0, 1)
+// (Newton's iteration for the inverse, quadratically convergent from the
+// float32-class X0).  The residuals are exact-slice products (5 slice levels
+// for R_0, 7 for R_1), the corrections split-bf16 products with float64
+// epilogues (X_k R_k is symmetric: lower triangle + mirror).  The last
+// correction is fused into its consumer:
+//  - gain_q != NULL (F = I, Q = q I or diagonal): J = I - Q X_2 into J64
+//    (float64) and Jf (float32), X_2 itself never stored;
+//  - gain_q == NULL: X_2 into X2 (float64, n x ldx).
+kf_status refine_inverse_tc(cudaStream_t s, TcScratch& sc, int n, const float* P, int64_t ldp, const float* W,
+                            int64_t ldw, RefineBufs& rb, int q_kind, const double* gain_q, double* J64, float* Jf,
+                            int64_t ldj, double* X2, int64_t ldx, int* status, int step);
 
 }  // namespace kfm

@@ -1,6 +1,8 @@
 // Tensor-core (tcgen05) split-bf16 GEMM used by the mixed-precision path.
 #pragma once
 
+#include <cuda.h>
+
 #include <functional>
 
 #include "ops.cuh"
@@ -34,6 +36,12 @@ constexpr uint64_t kTcDefaultWaitNs = 2000000000ull;
 
 // True when this build carries the tcgen05 kernels.
 bool tc_available();
+
+// 2-D TMA map of a bf16 matrix (rows x cols, leading dimension ld elements,
+// 16-byte aligned rows) with a box of box_cols x box_rows and the given
+// swizzle (64 or 128 bytes; the box row must be that wide).
+kf_status tma_map_bf16(CUtensorMap* map, const void* ptr, int64_t rows, int64_t cols, int64_t ld, int box_cols,
+                       int box_rows, int swizzle_bytes);
 
 // C = op(A) op(B) for float32 operands: A is M x K (or K x M with g.transA),
 // B is N x K when transB (C = A B^T) or K x N otherwise.  Each operand is
