@@ -140,7 +140,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp32", "fp64"])
-    ap.add_argument("--solve", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--solve", default="fp32", choices=["fp32", "fp64", "fp64tc"],
+                    help="smoother-gain solve: float32 class, float64 on the CUDA cores, or float64-accurate on "
+                         "the tensor cores (float32-class factor + Newton steps with exact-slice residuals)")
     ap.add_argument("--T", type=int, default=T_STEPS, help="time steps per epoch (the workload uses 300)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-plain", action="store_true")
@@ -276,7 +278,7 @@ def main():
     build.build()
     B.lib()
     prec = {"mixed": B.KF_PREC_MIXED_BF16X3, "fp32": B.KF_PREC_FP32, "fp64": B.KF_PREC_FP64}[args.prec]
-    solve = {"fp32": B.KF_SOLVE_FP32, "fp64": B.KF_SOLVE_FP64}[args.solve]
+    solve = {"fp32": B.KF_SOLVE_FP32, "fp64": B.KF_SOLVE_FP64, "fp64tc": B.KF_SOLVE_FP64_TC}[args.solve]
     T = args.T
     prob = synth.config2(T=T)
     d = solver.upload(prob)
@@ -308,7 +310,7 @@ def main():
         dist.barrier()
     elapsed = ev0.elapsed_time(ev1) / 1e3
     launches = B.kf_plan_launch_count(plan.handle) - launches0
-    prof = {c: B.kf_plan_profile_read(plan.handle, c) for c in range(8)}
+    prof = {c: B.kf_plan_profile_read(plan.handle, c) for c in range(9)}
     B.kf_plan_profile(plan.handle, False)
     if world > 1:
         t = torch.tensor([elapsed], device="cuda", dtype=torch.float64)
@@ -380,7 +382,7 @@ def main():
     if roof_solve["achieved"] is not None:
         roof_solve["frac"] = roof_solve["achieved"] / roof_solve["peak"]
     names = {0: "filter_update", 1: "innovation", 2: "smoother_gemm", 3: "smoother_solve", 4: "predict",
-             5: "solve_factor", 6: "solve_gain", 7: "smoother_gemm_kernel"}
+             5: "solve_factor", 6: "solve_gain", 7: "smoother_gemm_kernel", 8: "solve_refine"}
 
     line = {"metric": METRIC, "value": value, "unit": "timesteps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -393,7 +395,8 @@ def main():
                        "joseph_every": 16 if args.prec == "mixed" else 0,
                        "parallelism": f"replicas{world}",
                        "l2": "working set > L2 (covariance store of T N x N matrices)"},
-            "tflops": value * executed_flops_per_timestep(N, m, 16 if args.prec == "mixed" else 0) / 1e12,
+            "tflops": value * executed_flops_per_timestep(N, m, 16 if args.prec == "mixed" else 0,
+                                                          2 if args.solve == "fp64tc" else 0) / 1e12,
             "tflops_note": "flops the path executes (each split-bf16 product counted once)",
             "tflops_equivalent": value * total_f / 1e12,
             "tflops_equivalent_note": "standard operation count of KF + FIS (Cholesky + two N-RHS solves "

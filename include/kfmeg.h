@@ -63,10 +63,17 @@ typedef enum {
 } kf_precision;
 
 /* Arithmetic of the smoother-gain solve J_t = P_{t|t} F^T P_{t+1|t}^{-1}
- * (blocked Cholesky of P_{t+1|t} and two triangular solves). */
+ * (eqn 11: Cholesky of P_{t+1|t} and two triangular solves, or the inverse). */
 typedef enum {
-  KF_SOLVE_FP64 = 0,         /* float64 Cholesky and triangular solves               */
-  KF_SOLVE_FP32 = 1          /* float32 Cholesky and triangular solves               */
+  KF_SOLVE_FP64 = 0,         /* float64 Cholesky and triangular solves on the CUDA   */
+                             /* cores                                                */
+  KF_SOLVE_FP32 = 1,         /* float32 class: float32 factor (split-bf16 tensor-core */
+                             /* products in KF_PREC_MIXED_BF16X3)                    */
+  KF_SOLVE_FP64_TC = 2       /* float64 accuracy on the tensor cores (needs          */
+                             /* KF_PREC_MIXED_BF16X3): the float32-class inverse of  */
+                             /* P_{t+1|t} refined by two Newton steps whose residuals */
+                             /* I - P X are exact-slice products (kfx_spd_inverse    */
+                             /* mode 2); J_t in float64 for the smoothed mean        */
 } kf_solve_precision;
 
 typedef enum { KF_COV_SCALAR = 0, KF_COV_DIAG = 1, KF_COV_DENSE = 2 } kf_cov_kind;
@@ -197,7 +204,9 @@ typedef enum {
   KF_KC_SOLVE_GAIN = 6,      /* inside SMOOTH_SOLVE: forming J_t from the factor   */
   KF_KC_SMOOTH_GEMM_KERNEL = 7, /* inside SMOOTH_GEMM, mixed mode: the tensor-core */
                              /* kernel launches alone (one mark per launch)        */
-  KF_KC_COUNT = 8
+  KF_KC_SOLVE_REFINE = 8,    /* inside SOLVE_GAIN, KF_SOLVE_FP64_TC: the Newton      */
+                             /* refinement of the inverse of P_{t+1|t}             */
+  KF_KC_COUNT = 9
 } kf_kernel_class;
 kf_status kf_plan_profile(kf_plan_t p, int32_t enable);
 kf_status kf_plan_profile_read(kf_plan_t p, int32_t cls, int64_t* launches,

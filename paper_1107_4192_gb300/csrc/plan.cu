@@ -41,6 +41,7 @@ struct kf_plan_s {
   cudaStream_t s = nullptr;
   int64_t N = 0, m = 0, T = 0, ldN = 0, ldm = 0;
   int bulk = 0, solve = 0;
+  bool refine = false;    // KF_SOLVE_FP64_TC: float64-accurate inverse of P_{t+1|t}
   int smooth_slices = 2;  // bf16 planes per operand in the smoother products (mixed mode)
   size_t b = 8, sb = 8;   // bytes per bulk / solve element
   int64_t ckpt = 1;       // 1 = every P_{t|t} stored
@@ -58,6 +59,8 @@ struct kf_plan_s {
   char *Sl = nullptr, *Sldinv = nullptr;
   char *Lb = nullptr, *Ldinv = nullptr, *Jb = nullptr;
   float* Wi = nullptr;    // L^{-1} for the tensor-core solve (mixed mode, float32 solve)
+  RefineBufs rb{};        // refinement buffers (KF_SOLVE_FP64_TC)
+  double* J64 = nullptr;  // float64 J_t (KF_SOLVE_FP64_TC)
   double *P64 = nullptr, *W64 = nullptr, *U64 = nullptr, *Z64 = nullptr;  // float64 first update
   // The Cholesky + inverse of P_{t+1|t} is the same launch sequence at every
   // smoother step (only the step number differs, which kernels read from the
@@ -106,7 +109,7 @@ struct Sizes {
 Sizes sizes_for(const kf_desc* d) {
   Sizes z;
   z.b = d->prec == KF_PREC_FP64 ? 8 : 4;
-  z.sb = (d->prec == KF_PREC_FP64 || d->solve_prec == KF_SOLVE_FP64) ? 8 : 4;
+  z.sb = (d->prec == KF_PREC_FP64 || d->solve_prec == KF_SOLVE_FP64) ? 8 : 4;  // KF_SOLVE_FP64_TC: float32 factor
   z.ldN = round_up(d->N, 128);
   z.ldm = round_up(d->m, 64);
   const uint64_t N = d->N, m = d->m, T = d->T, ldN = z.ldN, ldm = z.ldm;
@@ -122,6 +125,7 @@ Sizes sizes_for(const kf_desc* d) {
   w += 2 * N * ldN * z.sb + round_up(N, nbs) * nbs * z.sb;                 // Lb, Jb, Ldinv
   w += (z.sb != z.b ? z.slot : 0) + 3 * z.slot;                            // Jm, Wb, Db, Pn
   if (d->prec == KF_PREC_MIXED_BF16X3 && z.sb == 4) w += z.slot;         // Wi
+  if (d->solve_prec == KF_SOLVE_FP64_TC) w += refine_bytes(N, ldN) + N * ldN * 8;  // refinement, J in float64
   if (z.b == 4) w += N * ldN * 8 * (d->f_kind != KF_F_IDENTITY ? 2 : 1) + 2 * N * ldm * 8;  // first update
   w += 3 * (T + 1) * N * 8 + m * 8 + N * 8;                                // means
   if (d->f_kind == KF_F_CSR) w += d->f_nnz * 16 + (N + 1) * 8;
@@ -141,7 +145,8 @@ kf_status validate(const kf_desc* d) {
   if (d->f_kind < 0 || d->f_kind > 2) return KF_ERR_ARG;
   if (d->f_kind == KF_F_CSR && d->f_nnz < 1) return KF_ERR_ARG;
   if (d->prec < 0 || d->prec > 2) return KF_ERR_ARG;
-  if (d->solve_prec < 0 || d->solve_prec > 1) return KF_ERR_ARG;
+  if (d->solve_prec < 0 || d->solve_prec > 2) return KF_ERR_ARG;
+  if (d->solve_prec == KF_SOLVE_FP64_TC && d->prec != KF_PREC_MIXED_BF16X3) return KF_ERR_ARG;
   if (d->q_kind < 0 || d->q_kind > 2 || d->r_kind < 0 || d->r_kind > 2) return KF_ERR_ARG;
   if (d->joseph_every < 0 || d->checkpoint_every < 0) return KF_ERR_ARG;
   if (d->split_terms != 0 && d->split_terms != 3 && d->split_terms != 6) return KF_ERR_ARG;
@@ -757,7 +762,23 @@ kf_status run_smoother(kf_plan_s* p, double* x_smooth, double* diagP_smooth, dou
         Bm = (const B*)p->tmpN;
       }
       Prof pg(p, KF_KC_SOLVE_GAIN);
-      if (tc_solve && p->d.f_kind == KF_F_IDENTITY && p->d.q_kind != KF_COV_DENSE) {
+      if (tc_solve && p->refine) {
+        // float64-accurate P_{t+1|t}^{-1} from the float32-class factor; J_t in float64 (mean) and
+        // float32 (covariance products)
+        Prof pr(p, KF_KC_SOLVE_REFINE);
+        const bool ident = p->d.f_kind == KF_F_IDENTITY && p->d.q_kind != KF_COV_DENSE;
+        KF_TRY(refine_inverse_tc(s, p->tc, (int)N, (const float*)Pn, ldN, p->Wi, ldN, p->rb, p->d.q_kind,
+                                 ident ? p->Q : nullptr, p->J64, (float*)Jb, ldN, p->rb.X0, ldN, p->status,
+                                 (int)(t + 1)));
+        if (!ident) {
+          GemmParams<double> g;  // J = (P_{t|t} F^T) X, X = P_{t+1|t}^{-1} symmetric (its rows are its columns)
+          g.M = (int)N; g.N = (int)N; g.K = (int)N;
+          g.out = p->J64; g.ldo = ldN;
+          g.outf = (float*)Jb; g.ldof = ldN;
+          g.status = p->status;
+          KF_TRY(tc_gemm_ops(s, p->tc, TcOperand{Bm, ldN, 0, 0}, TcOperand{p->rb.X0, ldN, 1, 0}, g, 3));
+        }
+      } else if (tc_solve && p->d.f_kind == KF_F_IDENTITY && p->d.q_kind != KF_COV_DENSE) {
         KF_TRY(gain_identity_tc(s, p->tc, (int)N, p->Wi, ldN, p->d.q_kind, p->Q, (float*)Jb, ldN, p->status));
       } else if (tc_solve) {
         if (Bm != Pt) {  // Bm lives in tmpN, which the products below use as scratch
@@ -774,7 +795,10 @@ kf_status run_smoother(kf_plan_s* p, double* x_smooth, double* diagP_smooth, dou
     }
     // x_{t|T} = x_{t|t} + J_t (x_{t+1|T} - x_{t+1|t})
     KF_TRY(vsub(s, N, p->xs + (t + 1) * N, p->xpred + (t + 1) * N, p->dx));
-    KF_TRY(gemv<V>(s, N, N, Jb, ldN, p->dx, p->xfilt + t * N, 1.0, p->xs + t * N));
+    if (p->refine)
+      KF_TRY(gemv<double>(s, N, N, p->J64, ldN, p->dx, p->xfilt + t * N, 1.0, p->xs + t * N));
+    else
+      KF_TRY(gemv<V>(s, N, N, Jb, ldN, p->dx, p->xfilt + t * N, 1.0, p->xs + t * N));
     if ((void*)Jm != (void*)Jb) KF_TRY((copy2d<B, V>(s, Jm, ldN, Jb, ldN, N, N)));
     {
       Prof pr(p, KF_KC_SMOOTH_GEMM);
@@ -877,6 +901,7 @@ kf_status kf_plan(kf_plan_t* out, const kf_desc* d) {
   p->b = z.b; p->sb = z.sb;
   p->bulk = d->prec == KF_PREC_FP64 ? BULK_F64 : d->prec == KF_PREC_FP32 ? BULK_F32 : BULK_BF16X3;
   p->solve = z.sb == 8 ? 0 : 1;
+  p->refine = d->solve_prec == KF_SOLVE_FP64_TC;
   p->smooth_slices = d->split_terms == 6 ? 3 : 2;
   p->slot = z.slot;
   p->ckpt = c;
@@ -914,6 +939,12 @@ kf_status kf_plan(kf_plan_t* out, const kf_desc* d) {
   A(&p->Ldinv, round_up(N, nbs) * nbs * sb);
   if (sb != b) A(&p->Jm, p->slot);
   if (p->bulk == BULK_BF16X3 && sb == 4) A(&p->Wi, p->slot);
+  if (p->refine) {
+    char* rm = nullptr;
+    A(&rm, refine_bytes(N, ldN));
+    if (st == KF_OK) refine_layout(p->rb, rm, N, ldN);
+    A(&p->J64, N * ldN * 8);
+  }
   if (b == 4) {
     A(&p->P64, N * ldN * 8);
     if (d->f_kind != KF_F_IDENTITY) A(&p->W64, N * ldN * 8);

@@ -20,6 +20,7 @@ from paper_1107_4192_gb300 import solver, synth  # noqa: E402
 from tests.helpers import diag_of, rel_err_elementwise, rel_err_per_step, run_oracle  # noqa: E402
 
 MIXED = dict(prec=B.KF_PREC_MIXED_BF16X3, solve_prec=B.KF_SOLVE_FP32)
+MIXED64 = dict(prec=B.KF_PREC_MIXED_BF16X3, solve_prec=B.KF_SOLVE_FP64_TC)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -36,13 +37,13 @@ def oracle_T2():
     return run_oracle(synth.config2(T=2))
 
 
-@pytest.mark.parametrize("mode", ["mixed", "fp64"])
+@pytest.mark.parametrize("mode", ["mixed", "mixed_fp64tc", "fp64"])
 def test_fullsize_vs_oracle_prefix(oracle_T2, mode):
     prob = synth.config2(T=2)
-    kw = MIXED if mode == "mixed" else dict(prec=B.KF_PREC_FP64)
+    kw = {"mixed": MIXED, "mixed_fp64tc": MIXED64, "fp64": dict(prec=B.KF_PREC_FP64)}[mode]
     out = solver.run(prob, **kw)
     ref = oracle_T2
-    tm, td = (1e-4, 1e-3) if mode == "mixed" else (1e-10, 1e-10)
+    tm, td = (1e-4, 1e-3) if mode.startswith("mixed") else (1e-10, 1e-10)
     assert rel_err_per_step(out["x_filt"], ref["x_filt"]) <= tm
     assert rel_err_per_step(out["x_smooth"], ref["x_smooth"]) <= tm
     assert rel_err_elementwise(out["diagP_filt"], diag_of(ref["P_filt"])) <= td

@@ -66,7 +66,7 @@ def test_fp32_paths(solve, mesh):
     check(solver.run(prob, prec=B.KF_PREC_FP32, solve_prec=solve), run_oracle(prob), TOL_MEAN32, TOL_DIAG32)
 
 
-@pytest.mark.parametrize("solve", [B.KF_SOLVE_FP64, B.KF_SOLVE_FP32])
+@pytest.mark.parametrize("solve", [B.KF_SOLVE_FP64, B.KF_SOLVE_FP32, B.KF_SOLVE_FP64_TC])
 @pytest.mark.parametrize("mesh", [False, True])
 def test_mixed_bf16x3_paths(solve, mesh):
     """Split-bf16 tensor-core products with float32 accumulation, Joseph form every 4 steps."""
@@ -75,10 +75,11 @@ def test_mixed_bf16x3_paths(solve, mesh):
     check(out, run_oracle(prob), TOL_MEAN32, TOL_DIAG32)
 
 
+@pytest.mark.parametrize("solve", [B.KF_SOLVE_FP32, B.KF_SOLVE_FP64_TC])
 @pytest.mark.parametrize("N,m,T", [(129, 20, 4), (257, 70, 5), (600, 64, 4), (200, 306, 5), (512, 306, 6)])
-def test_mixed_ragged_sizes(N, m, T):
+def test_mixed_ragged_sizes(N, m, T, solve):
     prob = synth.random_walk_problem(N, m, T, seed=N + m)
-    out = solver.run(prob, prec=B.KF_PREC_MIXED_BF16X3, solve_prec=B.KF_SOLVE_FP32, joseph_every=2)
+    out = solver.run(prob, prec=B.KF_PREC_MIXED_BF16X3, solve_prec=solve, joseph_every=2)
     check(out, run_oracle(prob), TOL_MEAN32, TOL_DIAG32)
 
 
@@ -125,7 +126,8 @@ def test_mixed_checkpoint_recompute(mesh, c):
     (B.KF_PREC_FP64, B.KF_SOLVE_FP64, TOL64, TOL64),
     (B.KF_PREC_FP32, B.KF_SOLVE_FP64, TOL_MEAN32, TOL_DIAG32),
     (B.KF_PREC_MIXED_BF16X3, B.KF_SOLVE_FP32, TOL_MEAN32, TOL_DIAG32),
-    (B.KF_PREC_MIXED_BF16X3, B.KF_SOLVE_FP64, TOL_MEAN32, TOL_DIAG32)])
+    (B.KF_PREC_MIXED_BF16X3, B.KF_SOLVE_FP64, TOL_MEAN32, TOL_DIAG32),
+    (B.KF_PREC_MIXED_BF16X3, B.KF_SOLVE_FP64_TC, TOL_MEAN32, TOL_DIAG32)])
 @pytest.mark.parametrize("N,m,T", [(200, 20, 8), (257, 70, 5)])
 def test_dense_F(prec, solve, tm, td, N, m, T):
     """General dense, non-symmetric F passed as a dense N x N matrix (KF_F_DENSE), dense Q, R, P0."""
