@@ -116,6 +116,13 @@ kf_status gemv(cudaStream_t s, int64_t rows, int64_t cols, const T* A, int64_t l
 // status[ST_CUR] = step (read by graph-replayed kernels that report failures)
 kf_status set_status_step(cudaStream_t s, int* status, int step);
 
+// dst = I (n x n, leading dimension ld), float64.
+kf_status eye(cudaStream_t s, int64_t n, double* dst, int64_t ld);
+
+// dst[j][i] = src[i][j] for a rows x cols float64 src.
+kf_status transpose(cudaStream_t s, int64_t rows, int64_t cols, const double* src, int64_t lds, double* dst,
+                    int64_t ldd);
+
 // d[i] = a[i] - b[i]
 kf_status vsub(cudaStream_t s, int64_t n, const double* a, const double* b, double* d);
 

@@ -60,8 +60,43 @@ struct OzMaps {
   CUtensorMap a, b;  // all slice planes of A (box 32 x 128) and of B (box 32 x 64)
 };
 
+// Full epilogue of element (gi, gj), gi >= gj when sym, from its product value c.
+__device__ __forceinline__ double oz_qv(int kind, const double* q, int64_t ldq, int i, int j) {
+  if (kind == 0) return i == j ? q[0] : 0.0;
+  if (kind == 1) return i == j ? q[i] : 0.0;
+  if (kind == 2) return q[(int64_t)i * ldq + j];
+  return 0.0;
+}
+
+__device__ __forceinline__ void oz_apply(const OzEpilogue& e, int gi, int gj, double c) {
+  double v = e.alpha * c;
+  if (e.cin) v += e.beta * e.cin[(int64_t)gi * e.ldcin + gj];
+  if (gi == gj) v += e.delta;
+  if (e.radd_kind >= 0) v += oz_qv(e.radd_kind, e.radd, e.ldradd, gi, gj);
+  const bool mirror = e.sym && gi != gj;
+  if (e.out) {
+    e.out[(int64_t)gi * e.ldo + gj] = v;
+    if (mirror) e.out[(int64_t)gj * e.ldo + gi] = v;
+  }
+  if (e.outf) {
+    e.outf[(int64_t)gi * e.ldof + gj] = (float)v;
+    if (mirror) e.outf[(int64_t)gj * e.ldof + gi] = (float)v;
+  }
+  if (e.outT) e.outT[(int64_t)gj * e.ldoT + gi] = v;
+  if (e.out2) {
+    e.out2[(int64_t)gi * e.ldo2 + gj] = v + oz_qv(e.q_kind, e.q, e.ldq, gi, gj);
+    if (mirror) e.out2[(int64_t)gj * e.ldo2 + gi] = v + oz_qv(e.q_kind, e.q, e.ldq, gj, gi);
+  }
+  if (gi == gj) {
+    if (e.diag_out) e.diag_out[gi] = v;
+    if (e.check_diag && !(v > 0.0 && isfinite(v))) status_set(e.status, KF_ERR_NUMERIC, e.step, gi);
+  }
+}
+
 struct OzArgs {
-  int M, N, nk;                  // nk = k-slices of OZ_BK
+  int M, N, nk;                  // nk = k-slices of OZ_BK this CTA sums (its split's share)
+  int kt_per_split;              // k-slices per split (blockIdx.y)
+  double* partials;              // splits > 1: raw sums, split s at partials + s M N (ld N)
   int a_rows_pad, b_rows_pad;    // plane p starts at row p * rows_pad of its map
   const int* ea;
   const int* eb;
@@ -119,6 +154,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
   const int gsize = min(tiles_m - first_m, OZ_GROUP);
   const int local = t - grp * per_group;
   const int m0 = (first_m + local % gsize) * OZ_BM, n0 = (local / gsize) * OZ_BN;
+  if (a.e.sym && m0 + OZ_BM - 1 < n0) return;  // tile entirely above the diagonal
+  // this CTA's k-slices: [kt0, kt0 + nk)
+  const int kt0 = blockIdx.y * a.kt_per_split;
+  const int nk = min(a.nk - kt0, a.kt_per_split);
 
   const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
   uint8_t* gbase = smem_raw + (base - smem_u32(smem_raw));
@@ -158,8 +197,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
-  const bool skip = *skip_flag != 0;
-  const int nk = a.nk;
+  const bool skip = *skip_flag != 0 || nk <= 0;
   const int nchunks = (nk + OZ_CK - 1) / OZ_CK;
   bool mma_issued = false;
 
@@ -178,7 +216,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
       }
       const uint32_t st = base + s * C::STAGE_BYTES;
       mbar_expect_tx(full_bar(s), C::STAGE_BYTES);
-      const int x = it * OZ_BK;
+      const int x = (kt0 + it) * OZ_BK;
 #pragma unroll
       for (int p = 0; p < LV; ++p) tma_load_2d(st + p * C::A_BYTES, &maps.a, x, p * a.a_rows_pad + m0, full_bar(s));
 #pragma unroll
@@ -269,18 +307,17 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
     }
     if (ok && !*abort_flag && gi < a.M) {
       const int ei = a.ea[gi];
-      const OzEpilogue& e = a.e;
+      double* part = a.partials ? a.partials + (int64_t)blockIdx.y * a.M * a.N : nullptr;
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
         const int gj = n0 + h * 16 + j;
-        if (gj < a.N) {
+        if (gj < a.N && !(a.e.sym && gj > gi)) {
           const int sc = ei + a.eb[gj] - 14;
           const double cval = scalbn((double)hi[j], sc - 16) + scalbn((double)lo[j], sc - 8 * (LV - 1));
-          double v = e.alpha * cval;
-          if (e.cin) v += e.beta * e.cin[(int64_t)gi * e.ldcin + gj];
-          if (gi == gj) v += e.delta;
-          e.out[(int64_t)gi * e.ldo + gj] = v;
-          if (e.outf) e.outf[(int64_t)gi * e.ldof + gj] = (float)v;
+          if (part)
+            part[(int64_t)gi * a.N + gj] = cval;
+          else
+            oz_apply(a.e, gi, gj, cval);
         }
       }
     }
@@ -298,8 +335,22 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
   }
 }
 
+// Sum of the split-K partials in split order, then the epilogue (one thread per element).
+__global__ void oz_reduce_kernel(int M, int N, int splits, const double* partials, OzEpilogue e) {
+  if (status_failed(e.status)) return;
+  const int64_t total = (int64_t)M * N;
+  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < total; u += (int64_t)gridDim.x * blockDim.x) {
+    const int gi = (int)(u / N), gj = (int)(u % N);
+    if (e.sym && gj > gi) continue;
+    double c = 0.0;
+    for (int sp = 0; sp < splits; ++sp) c += partials[(int64_t)sp * total + u];
+    oz_apply(e, gi, gj, c);
+  }
+}
+
 template <int LV>
-kf_status launch_oz(cudaStream_t s, const OzSlices& A, const OzSlices& B, int M, int N, int K, const OzEpilogue& e) {
+kf_status launch_oz(cudaStream_t s, const OzSlices& A, const OzSlices& B, int M, int N, int K, const OzEpilogue& e,
+                    int splits, double* partials) {
   using C = OzCfg<LV>;
   OzMaps maps;
   KF_TRY(tma_map_bf16(&maps.a, A.planes, (int64_t)A.S * A.rows_pad, A.ldk, A.ldk, OZ_BK, OZ_BM, 64));
@@ -308,6 +359,8 @@ kf_status launch_oz(cudaStream_t s, const OzSlices& A, const OzSlices& B, int M,
   a.M = M;
   a.N = N;
   a.nk = (int)ceil_div(K, OZ_BK);
+  a.kt_per_split = (int)ceil_div(a.nk, splits);
+  a.partials = splits > 1 ? partials : nullptr;
   a.a_rows_pad = (int)A.rows_pad;
   a.b_rows_pad = (int)B.rows_pad;
   a.ea = A.exps;
@@ -317,10 +370,17 @@ kf_status launch_oz(cudaStream_t s, const OzSlices& A, const OzSlices& B, int M,
   KF_CUDA_TRY(smem_limit_per_device((const void*)oz_gemm_kernel<LV>, (int)C::SMEM));
   const int64_t tiles = ceil_div(M, OZ_BM) * ceil_div(N, OZ_BN);
   if (g_tc_timer) g_tc_timer->before(s);
-  oz_gemm_kernel<LV><<<(unsigned)tiles, OZ_THREADS, C::SMEM, s>>>(maps, a);
+  oz_gemm_kernel<LV><<<dim3((unsigned)tiles, (unsigned)splits), OZ_THREADS, C::SMEM, s>>>(maps, a);
   if (g_tc_timer) g_tc_timer->after(s);
   note_launch();
-  return launch_check("oz_gemm");
+  KF_TRY(launch_check("oz_gemm"));
+  if (splits > 1) {
+    const int64_t total = (int64_t)M * N;
+    oz_reduce_kernel<<<(unsigned)std::min<int64_t>(ceil_div(total, 256), 4096), 256, 0, s>>>(M, N, splits, partials, e);
+    note_launch();
+    KF_TRY(launch_check("oz_reduce"));
+  }
+  return KF_OK;
 }
 
 }  // namespace
@@ -356,13 +416,19 @@ kf_status oz_slice(cudaStream_t s, const void* X, int64_t ld, int f64, int64_t r
 }
 
 kf_status oz_gemm(cudaStream_t s, const OzSlices& A, const OzSlices& B, int M, int N, int K, int levels,
-                  const OzEpilogue& e) {
+                  const OzEpilogue& e, int splits, double* partials) {
   if (M <= 0 || N <= 0) return KF_OK;
-  if (K < 1 || K > (1 << 20) || !e.out) return KF_ERR_ARG;
+  if (K < 1 || K > (1 << 20)) return KF_ERR_ARG;
+  if (!e.out && !e.outf && !e.outT && !e.out2 && !e.diag_out) return KF_ERR_ARG;
   if (M > A.rows || N > B.rows || K > A.ldk || K > B.ldk) return KF_ERR_ARG;
-  if (A.filled < levels || B.filled < levels) return KF_ERR_ARG;
-  if (levels == 5) return launch_oz<5>(s, A, B, M, N, K, e);
-  if (levels == 7) return launch_oz<7>(s, A, B, M, N, K, e);
+  if (A.filled < levels || B.filled < levels || (e.sym && M != N)) return KF_ERR_ARG;
+  if (splits < 1 || splits > 64 || (splits > 1 && !partials)) return KF_ERR_ARG;
+  // every split gets at least one k-slice
+  splits = (int)std::min<int64_t>(splits, ceil_div(K, OZ_BK));
+  const int kps = (int)ceil_div(ceil_div(K, OZ_BK), splits);
+  splits = (int)ceil_div(ceil_div(K, OZ_BK), kps);
+  if (levels == 5) return launch_oz<5>(s, A, B, M, N, K, e, splits, partials);
+  if (levels == 7) return launch_oz<7>(s, A, B, M, N, K, e, splits, partials);
   return KF_ERR_ARG;
 }
 

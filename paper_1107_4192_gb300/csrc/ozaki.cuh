@@ -44,9 +44,14 @@ void oz_slice_layout(OzSlices& out, void* mem, int64_t rows, int64_t cols, int S
 kf_status oz_slice(cudaStream_t s, const void* X, int64_t ld, int f64, int64_t rows, int64_t cols, int S,
                    OzSlices& out);
 
-// Epilogue of the exact-slice product, float64:
-//   out[i][j] = alpha * (A B^T)[i][j] + beta * cin[i][j] + (i == j ? delta : 0)
-// (cin optional); outf (optional) receives a float32 copy.
+// Epilogue of the exact-slice product, float64.  With acc = (A B^T)[i][j]:
+//   v = alpha acc + beta cin[i][j] + (i == j ? delta : 0) + Radd[i][j]
+//   out[i][j] = v,  outf[i][j] = (float) v,  outT[j][i] = v,
+//   out2[i][j] = v + Q[i][j],  diag_out[i] = v at i == j
+// (each optional; Radd per radd_kind and Q per q_kind as kf_cov_kind, < 0 =
+// none).  check_diag: a diagonal v that is not finite and > 0 raises
+// KF_ERR_NUMERIC at `step`.  sym (M == N): only i >= j is computed and out,
+// outf and out2 are mirrored to (j, i), so they come out exactly symmetric.
 struct OzEpilogue {
   double alpha = 1.0, beta = 0.0, delta = 0.0;
   const double* cin = nullptr;
@@ -55,14 +60,29 @@ struct OzEpilogue {
   int64_t ldo = 0;
   float* outf = nullptr;
   int64_t ldof = 0;
+  double* outT = nullptr;
+  int64_t ldoT = 0;
+  double* out2 = nullptr;
+  int64_t ldo2 = 0;
+  int q_kind = -1;
+  const double* q = nullptr;
+  int64_t ldq = 0;
+  int radd_kind = -1;
+  const double* radd = nullptr;
+  int64_t ldradd = 0;
+  double* diag_out = nullptr;
+  int check_diag = 0;
+  int sym = 0;
   int* status = nullptr;  // KF_ERR_TIMEOUT on an expired wait; kernels skip when already failed
   int step = 0;
 };
 
 // C = A B^T for A (M x K) and B (N x K) given by their slices, keeping the
 // slice levels l < levels (5 or 7; both operands need at least `levels`
-// slices).  K <= 2^20.
+// slices).  K <= 2^20.  splits > 1 divides K among that many CTAs per output
+// tile, whose float64 partial sums (splits x M x N doubles at `partials`) are
+// added in a fixed order by a second kernel that applies the epilogue.
 kf_status oz_gemm(cudaStream_t s, const OzSlices& A, const OzSlices& B, int M, int N, int K, int levels,
-                  const OzEpilogue& e);
+                  const OzEpilogue& e, int splits = 1, double* partials = nullptr);
 
 }  // namespace kfm

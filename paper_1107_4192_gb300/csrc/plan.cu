@@ -32,7 +32,9 @@ struct ProfMark {
   cudaEvent_t a, b;
 };
 
-constexpr int kSplitsS = 8;  // split-K factor of S = H U^T
+constexpr int kSplitsS = 8;   // split-K factor of S = H U^T (CUDA-core paths)
+constexpr int kOzSplitsS = 16;  // split-K factor of S = H U^T (exact-slice product)
+constexpr int kOzLevels = 5;    // slice levels of the mixed filter's products (about 2^-37 of |A||B|)
 
 }  // namespace
 
@@ -61,7 +63,12 @@ struct kf_plan_s {
   float* Wi = nullptr;    // L^{-1} for the tensor-core solve (mixed mode, float32 solve)
   RefineBufs rb{};        // refinement buffers (KF_SOLVE_FP64_TC)
   double* J64 = nullptr;  // float64 J_t (KF_SOLVE_FP64_TC)
-  double *P64 = nullptr, *W64 = nullptr, *U64 = nullptr, *Z64 = nullptr;  // float64 first update
+  double *P64 = nullptr, *W64 = nullptr, *U64 = nullptr, *Z64 = nullptr;  // float64 working covariance / first update
+  // Mixed filter (exact-slice products): U = H P (m x N, besides U^T in U64), L^{-1} and L^{-T} of the
+  // innovation factor, [K V] and [V K] of the Joseph form, split-K partials of S, the slices of every
+  // operand (5 levels), and a device 1.0 for identities.
+  double *Um = nullptr, *Linv = nullptr, *LinvT = nullptr, *KV64 = nullptr, *VK64 = nullptr, *ozpart = nullptr;
+  OzSlices sP, sH, sU, sUt, sL, sLT, sZ, sK, sS0, sKV, sVK;
   // The Cholesky + inverse of P_{t+1|t} is the same launch sequence at every
   // smoother step (only the step number differs, which kernels read from the
   // status word), so it is captured once into a CUDA graph and replayed.
@@ -126,6 +133,13 @@ Sizes sizes_for(const kf_desc* d) {
   w += (z.sb != z.b ? z.slot : 0) + 3 * z.slot;                            // Jm, Wb, Db, Pn
   if (d->prec == KF_PREC_MIXED_BF16X3 && z.sb == 4) w += z.slot;         // Wi
   if (d->solve_prec == KF_SOLVE_FP64_TC) w += refine_bytes(N, ldN) + N * ldN * 8;  // refinement, J in float64
+  if (d->prec == KF_PREC_MIXED_BF16X3) {
+    // exact-slice filter: U, L^{-1}, L^{-T}, [K V], [V K], S partials, slices
+    w += m * ldN * 8 + 2 * m * m * 8 + (d->joseph_every > 0 ? 4 * N * ldm * 8 : 0) + kOzSplitsS * m * m * 8 + 8;
+    const int S = kOzLevels;
+    w += oz_slice_bytes(N, N, S) + 2 * oz_slice_bytes(m, N, S) + 3 * oz_slice_bytes(N, m, S) +
+         3 * oz_slice_bytes(m, m, S) + (d->joseph_every > 0 ? 2 * oz_slice_bytes(N, 2 * ldm, S) : 0) + 12 * 256;
+  }
   if (z.b == 4) w += N * ldN * 8 * (d->f_kind != KF_F_IDENTITY ? 2 : 1) + 2 * N * ldm * 8;  // first update
   w += 3 * (T + 1) * N * 8 + m * 8 + N * 8;                                // means
   if (d->f_kind == KF_F_CSR) w += d->f_nnz * 16 + (N + 1) * 8;
@@ -445,47 +459,63 @@ kf_status predict_cov64(kf_plan_s* p, double* P) {
 }
 
 // One filter step of the mixed mode.  The working covariance P_{t|t-1} is
-// kept in float64 (p->P64): its well-observed directions have variances far
-// below its others, so float32 storage alone would limit the filter to about
-// 1e-4 relative accuracy at N ~ 10^4.  Products are three-way split-bf16 on
-// the tensor cores (float32-class), added to the float64 P in the epilogue;
-// P_{t|t} is rounded to float32 only for the smoother's store.
+// kept in float64 (p->P64) and every product of the step is an exact-slice
+// tensor-core product (5 slice levels: about 2^-37 of the operands' row
+// maxima, far below float32 rounding) with a float64 epilogue: the filter
+// runs at float64-class accuracy, which a long epoch needs because rounding
+// errors of P in the directions the sensors do not see are never damped (F = I)
+// and the mean integrates the resulting gain errors.  P_{t|t} is rounded to
+// float32 only for the smoother's store.
+//   U^T = P H^T (N x m) and U (m x N);  S = H U^T + R;  S = L L^T (float64);
+//   Z = U^T L^{-T};  x += Z (L^{-1} nu);  P_{t|t} = P - Z Z^T (or Joseph form)
 kf_status filter_step_mixed(kf_plan_s* p, int64_t t, const double* y, double* diag_out) {
   cudaStream_t s = p->s;
   const int N = (int)p->N, m = (int)p->m;
   const int64_t ldN = p->ldN, ldm = p->ldm, ldkv = 2 * p->ldm;
+  const int LV = kOzLevels;
   double* P = p->P64;
-  float* Ut = (float*)p->Ut;
+  double* Ut = p->U64;
   {
     Prof pr(p, KF_KC_INNOVATION);
-    GemmParams<float> g;  // U^T = P H^T
-    g.M = N; g.N = m; g.K = N;
-    g.out = Ut; g.ldo = ldm;
-    g.status = p->status;
-    KF_TRY(tc_gemm_ops(s, p->tc, TcOperand{P, ldN, 1, 0}, TcOperand{p->H, N, 1, 0}, g, 3));
+    KF_TRY(oz_slice(s, P, ldN, 1, N, N, LV, p->sP));
+    OzEpilogue e;  // U^T = P H^T, and its transpose U
+    e.out = Ut; e.ldo = ldm;
+    e.outT = p->Um; e.ldoT = ldN;
+    e.status = p->status; e.step = (int)t;
+    KF_TRY(oz_gemm(s, p->sP, p->sH, N, m, N, LV, e));
   }
-  // H's float copy: the products are float32 either way
-  KF_TRY((innovation_cov<float, float>(s, m, N, (const float*)p->Hb, p->ldN, Ut, ldm, p->d.r_kind, p->R, p->S, m,
-                                      p->partials, kSplitsS)));
+  {
+    KF_TRY(oz_slice(s, p->Um, ldN, 1, m, N, LV, p->sU));
+    OzEpilogue e;  // S = H U^T + R (exactly symmetric)
+    e.out = p->S; e.ldo = m;
+    e.radd_kind = p->d.r_kind; e.radd = p->R; e.ldradd = m;
+    e.sym = 1;
+    e.status = p->status; e.step = (int)t;
+    KF_TRY(oz_gemm(s, p->sH, p->sU, m, m, N, LV, e, kOzSplitsS, p->ozpart));
+  }
   const bool joseph = p->d.joseph_every > 0 && (t % p->d.joseph_every) == 0;
   if (joseph) KF_CUDA_TRY(cudaMemcpyAsync(p->S0, p->S, (size_t)m * m * 8, cudaMemcpyDeviceToDevice, s));
   const int nbS = kSBlock;
   KF_TRY(potrf<double>(s, p->S, m, m, p->Sdinv, nbS, p->status, (int)t));
-  KF_TRY((copy2d<float, double>(s, (float*)p->Sl, m, p->S, m, m, m)));
-  KF_TRY((copy2d<float, double>(s, (float*)p->Sldinv, nbS, p->Sdinv, nbS, round_up(m, nbS), nbS)));
-  const float* L = (const float*)p->Sl;
-  const float* Ld = (const float*)p->Sldinv;
-  float* Z = (float*)p->Zb;  // Z = U^T L^{-T}
-  KF_TRY((copy2d<float, float>(s, Z, ldm, Ut, ldm, N, m)));
-  KF_TRY(trsm_right<float>(s, true, N, m, L, m, Ld, nbS, Z, ldm, p->status));
+  // L^{-1} = I L^{-1} (m x m, float64)
+  KF_TRY(eye(s, m, p->Linv, m));
+  KF_TRY(trsm_right<double>(s, false, m, m, p->S, m, p->Sdinv, nbS, p->Linv, m, p->status));
+  double* Z = p->Z64;
+  {
+    KF_TRY(oz_slice(s, Ut, ldm, 1, N, m, LV, p->sUt));
+    KF_TRY(oz_slice(s, p->Linv, m, 1, m, m, LV, p->sL));
+    OzEpilogue e;  // Z = U^T L^{-T}:  Z[n][i] = sum_k U^T[n][k] L^{-1}[i][k]
+    e.out = Z; e.ldo = ldm;
+    e.status = p->status; e.step = (int)t;
+    KF_TRY(oz_gemm(s, p->sUt, p->sL, N, m, m, LV, e));
+  }
   if (y) {
     KF_TRY(innovation(s, m, N, p->H, p->xpred + t * N, y, p->nu, p->status, (int)t));
     KF_TRY(trsm_right<double>(s, true, 1, m, p->S, m, p->Sdinv, nbS, p->nu, m, p->status));
-    KF_TRY(gemv<float>(s, N, m, Z, ldm, p->nu, p->xpred + t * N, 1.0, p->xfilt + t * N));
+    KF_TRY(gemv<double>(s, N, m, Z, ldm, p->nu, p->xpred + t * N, 1.0, p->xfilt + t * N));
   }
   const bool ident = p->d.f_kind == KF_F_IDENTITY;
-  GemmParams<double> u;  // P_{t|t} = P - Z Z^T (float64 result, float32 copy to the store)
-  u.M = N; u.N = N;
+  OzEpilogue u;  // P_{t|t} = P - Z Z^T: float64 result, float32 copy to the store
   u.alpha = -1.0;
   u.cin = P; u.ldcin = ldN; u.beta = 1.0;
   u.outf = (float*)p->slot_ptr(t); u.ldof = ldN;
@@ -497,38 +527,64 @@ kf_status filter_step_mixed(kf_plan_s* p, int64_t t, const double* y, double* di
   }
   u.diag_out = diag_out;
   u.check_diag = 1;
-  u.step = (int)t;
-  u.status = p->status;
   u.sym = 1;
-  TcOperand ua{Z, ldm, 0, 0}, ub{Z, ldm, 0, 0};
-  u.K = (int)ldm;
-  if (joseph) {
-    float* KV = (float*)p->KV;
-    float* VK = (float*)p->VK;
-    KF_TRY((copy2d<float, float>(s, KV, ldkv, Z, ldm, N, m)));
-    KF_TRY(trsm_right<float>(s, false, N, m, L, m, Ld, nbS, KV, ldkv, p->status));
-    KF_TRY((copy2d<float, double>(s, (float*)p->S0b, m, p->S0, m, m, m)));
-    GemmParams<float> v;  // V = U^T - K S / 2
-    v.M = N; v.N = m; v.K = m;
-    v.A = KV; v.lda = ldkv;
-    v.B = (const float*)p->S0b; v.ldb = m;
-    v.alpha = -0.5f;
-    v.cin = Ut; v.ldcin = ldm; v.beta = 1.0f;
-    v.out = KV + ldm; v.ldo = ldkv;
-    v.status = p->status;
-    KF_TRY(gemm_simt<float>(s, true, v));
-    KF_TRY((copy2d<float, float>(s, VK, ldkv, KV + ldm, ldkv, N, m)));
-    KF_TRY((copy2d<float, float>(s, VK + ldm, ldkv, KV, ldkv, N, m)));
-    ua = TcOperand{KV, ldkv, 0, 0};
-    ub = TcOperand{VK, ldkv, 0, 0};
-    u.K = (int)ldkv;
-  }
-  {
-    Prof pr(p, KF_KC_FILTER_UPDATE);
-    KF_TRY(tc_gemm_ops(s, p->tc, ua, ub, u, 3));
+  u.status = p->status; u.step = (int)t;
+  Prof pr(p, KF_KC_FILTER_UPDATE);
+  if (!joseph) {
+    KF_TRY(oz_slice(s, Z, ldm, 1, N, m, LV, p->sZ));
+    KF_TRY(oz_gemm(s, p->sZ, p->sZ, N, N, m, LV, u));
+  } else {
+    // Joseph form (I - KH) P (I - KH)^T + K R K^T = P - K V^T - V K^T with K = Z L^{-1} and
+    // V = U^T - K S / 2: one rank-2m product [K V][V K]^T.
+    double* KV = p->KV64;
+    double* VK = p->VK64;
+    KF_TRY(oz_slice(s, Z, ldm, 1, N, m, LV, p->sZ));
+    KF_TRY(transpose(s, m, m, p->Linv, m, p->LinvT, m));
+    KF_TRY(oz_slice(s, p->LinvT, m, 1, m, m, LV, p->sLT));
+    OzEpilogue ek;  // K[n][i] = sum_k Z[n][k] L^{-1}[k][i]
+    ek.out = KV; ek.ldo = ldkv;
+    ek.status = p->status; ek.step = (int)t;
+    KF_TRY(oz_gemm(s, p->sZ, p->sLT, N, m, m, LV, ek));
+    KF_TRY(oz_slice(s, KV, ldkv, 1, N, m, LV, p->sK));
+    KF_TRY(oz_slice(s, p->S0, m, 1, m, m, LV, p->sS0));
+    OzEpilogue ev;  // V = U^T - K S / 2  (S symmetric: its rows are its columns)
+    ev.alpha = -0.5;
+    ev.cin = Ut; ev.ldcin = ldm; ev.beta = 1.0;
+    ev.out = KV + ldm; ev.ldo = ldkv;
+    ev.status = p->status; ev.step = (int)t;
+    KF_TRY(oz_gemm(s, p->sK, p->sS0, N, m, m, LV, ev));
+    KF_TRY((copy2d<double, double>(s, VK, ldkv, KV + ldm, ldkv, N, m)));
+    KF_TRY((copy2d<double, double>(s, VK + ldm, ldkv, KV, ldkv, N, m)));
+    KF_TRY(oz_slice(s, KV, ldkv, 1, N, ldkv, LV, p->sKV));
+    KF_TRY(oz_slice(s, VK, ldkv, 1, N, ldkv, LV, p->sVK));
+    KF_TRY(oz_gemm(s, p->sKV, p->sVK, N, N, (int)ldkv, LV, u));
   }
   if (!ident) KF_TRY(predict_cov64(p, P));
   return KF_OK;
+}
+
+// P_{1|0} = F P0 F^T + Q into the mixed filter's float64 working covariance.
+kf_status predict_first64(kf_plan_s* p, const double* P0) {
+  cudaStream_t s = p->s;
+  const int N = (int)p->N;
+  const int64_t ldN = p->ldN;
+  double* P = p->P64;
+  if (p->d.f_kind == KF_F_IDENTITY) return add_cov<double, double>(s, P, ldN, P0, N, N, p->d.q_kind, p->Q);
+  if (p->d.f_kind == KF_F_CSR)
+    return spmm_fpft<double>(s, N, p->Frp, p->Fcol, p->F, P0, N, p->W64, ldN, P, ldN, p->d.q_kind, p->Q);
+  GemmParams<double> g;  // W = F P0, then P = W F^T + Q
+  g.M = N; g.N = N; g.K = N;
+  g.A = p->F; g.lda = N;
+  g.B = P0; g.ldb = N;
+  g.out = p->W64; g.ldo = ldN;
+  KF_TRY(gemm_simt<double>(s, false, g));
+  GemmParams<double> h;
+  h.M = N; h.N = N; h.K = N;
+  h.A = p->W64; h.lda = ldN;
+  h.B = p->F; h.ldb = N;
+  h.out2 = P; h.ldo2 = ldN;
+  h.q_kind = p->d.q_kind; h.q = p->Q; h.ldq = N;
+  return gemm_simt<double>(s, true, h);
 }
 
 // The first update in float64 for the float32 stores.  P0 is usually far
@@ -593,7 +649,6 @@ kf_status filter_first_fp64(kf_plan_s* p, const double* P0, const double* y, dou
   KF_TRY(gemm_simt<double>(s, true, u));
   float* dst = (float*)p->slot_ptr(1);
   KF_TRY((copy2d<float, double>(s, dst, ldN, P, ldN, N, N)));
-  if (p->bulk == BULK_BF16X3) return predict_cov64(p, P);  // the mixed filter continues in float64
   if (p->d.f_kind == KF_F_IDENTITY) return add_cov<float, double>(s, (float*)p->P, ldN, P, ldN, N, p->d.q_kind, p->Q);
   return predict_cov<float>(p, dst, (float*)p->P);
 }
@@ -640,14 +695,19 @@ kf_status run_filter(kf_plan_s* p, const double* Y, const double* x0, const doub
   KF_CUDA_TRY(cudaMemcpyAsync(p->xfilt, x0, N * 8, cudaMemcpyDeviceToDevice, s));
   // P0 into store slot 0 (bulk dtype), then P_{1|0}
   KF_TRY((copy2d<B, double>(s, (B*)p->slot_ptr(0), p->ldN, P0, N, N, N)));
-  KF_TRY(predict_cov<B>(p, (const B*)p->slot_ptr(0), (B*)p->P));
+  if (p->bulk == BULK_BF16X3) {
+    KF_TRY(oz_slice(s, p->H, N, 1, m, N, kOzLevels, p->sH));  // the lead field's slices, once per epoch
+    KF_TRY(predict_first64(p, P0));
+  } else {
+    KF_TRY(predict_cov<B>(p, (const B*)p->slot_ptr(0), (B*)p->P));
+  }
   for (int64_t t = 1; t <= T; ++t) {
     KF_TRY(predict_mean(s, p->d.f_kind, N, p->F, p->Frp, p->Fcol, p->xfilt + (t - 1) * N, p->xpred + t * N));
     double* dg = diagP_filt ? diagP_filt + (t - 1) * N : nullptr;
-    if (t == 1 && sizeof(B) == 4)
-      KF_TRY(filter_first_fp64(p, P0, Y, dg));
-    else if (p->bulk == BULK_BF16X3)
+    if (p->bulk == BULK_BF16X3)
       KF_TRY(filter_step_mixed(p, t, Y + (t - 1) * m, dg));
+    else if (t == 1 && sizeof(B) == 4)
+      KF_TRY(filter_first_fp64(p, P0, Y, dg));
     else
       KF_TRY(filter_step<B>(p, t, Y + (t - 1) * m, dg));
     if (p->ckpt > 1 && t % p->ckpt != 0) p->seg_id = t / p->ckpt;
@@ -950,6 +1010,34 @@ kf_status kf_plan(kf_plan_t* out, const kf_desc* d) {
     if (d->f_kind != KF_F_IDENTITY) A(&p->W64, N * ldN * 8);
     A(&p->U64, N * ldm * 8);
     A(&p->Z64, N * ldm * 8);
+  }
+  if (p->bulk == BULK_BF16X3) {
+    A(&p->Um, m * ldN * 8);
+    A(&p->Linv, m * m * 8);
+    A(&p->LinvT, m * m * 8);
+    A(&p->ozpart, kOzSplitsS * m * m * 8);
+    if (d->joseph_every > 0) {
+      A(&p->KV64, N * 2 * ldm * 8);
+      A(&p->VK64, N * 2 * ldm * 8);
+    }
+    auto AS = [&](OzSlices& sl, int64_t rows, int64_t cols) {
+      char* mem = nullptr;
+      A(&mem, oz_slice_bytes(rows, cols, kOzLevels));
+      if (st == KF_OK) oz_slice_layout(sl, mem, rows, cols, kOzLevels);
+    };
+    AS(p->sP, N, N);
+    AS(p->sH, m, N);
+    AS(p->sU, m, N);
+    AS(p->sUt, N, m);
+    AS(p->sZ, N, m);
+    AS(p->sK, N, m);
+    AS(p->sL, m, m);
+    AS(p->sLT, m, m);
+    AS(p->sS0, m, m);
+    if (d->joseph_every > 0) {
+      AS(p->sKV, N, 2 * ldm);
+      AS(p->sVK, N, 2 * ldm);
+    }
   }
   A(&p->Wb, p->slot);
   A(&p->Db, p->slot);

@@ -564,6 +564,42 @@ kf_status split_bf16_pair(cudaStream_t s, const SplitOp& a, const SplitOp& b, in
   return launch_check("split_bf16_pair");
 }
 
+__global__ void eye_kernel(int64_t n, double* d, int64_t ld) {
+  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n * n; u += (int64_t)gridDim.x * blockDim.x)
+    d[(u / n) * ld + u % n] = (u / n == u % n) ? 1.0 : 0.0;
+}
+
+kf_status eye(cudaStream_t s, int64_t n, double* dst, int64_t ld) {
+  if (n <= 0) return KF_OK;
+  eye_kernel<<<(unsigned)std::min<int64_t>(ceil_div(n * n, 256), 4096), 256, 0, s>>>(n, dst, ld);
+  note_launch();
+  return launch_check("eye");
+}
+
+__global__ void transpose_kernel(int64_t rows, int64_t cols, const double* src, int64_t lds, double* dst,
+                                 int64_t ldd) {
+  __shared__ double tile[32][33];
+  const int64_t r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int64_t r = r0 + i, c = c0 + threadIdx.x;
+    tile[i][threadIdx.x] = (r < rows && c < cols) ? src[r * lds + c] : 0.0;
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int64_t c = c0 + i, r = r0 + threadIdx.x;
+    if (c < cols && r < rows) dst[c * ldd + r] = tile[threadIdx.x][i];
+  }
+}
+
+kf_status transpose(cudaStream_t s, int64_t rows, int64_t cols, const double* src, int64_t lds, double* dst,
+                    int64_t ldd) {
+  if (rows <= 0 || cols <= 0) return KF_OK;
+  transpose_kernel<<<dim3((unsigned)ceil_div(cols, 32), (unsigned)ceil_div(rows, 32)), dim3(32, 8), 0, s>>>(
+      rows, cols, src, lds, dst, ldd);
+  note_launch();
+  return launch_check("transpose");
+}
+
 template <typename T>
 __global__ void diag_kernel(int64_t n, const T* A, int64_t lda, double* d) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)

@@ -68,6 +68,7 @@ struct TcMaps {
 };
 
 constexpr int KC = 1;  // k-tiles accumulated in TMEM before promotion to registers
+constexpr int GROUP = 16;  // row tiles per rasterisation group
 
 // Epilogue threads: warps 2..9.  Warp w reads TMEM lanes 32*(w%4)..+31 (its
 // lane quadrant) and one half of the BN columns, so each output row is owned
@@ -78,7 +79,15 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   using C = TcCfg<BN, S>;
   constexpr int HALF = BN / 2;
   extern __shared__ uint8_t smem_raw[];
-  const int tn = blockIdx.x, tm = blockIdx.y;
+  // grouped rasterisation: consecutive CTAs sweep the column tiles of GROUP row tiles together, so a
+  // wave of CTAs reads about GROUP row tiles of A and 152 / GROUP column tiles of B from DRAM per k-tile
+  // instead of a few row tiles and every column tile of B
+  const int tiles_m = (p.M + BM - 1) / BM, tiles_n = (p.N + BN - 1) / BN;
+  const int per_group = GROUP * tiles_n;
+  const int grp = blockIdx.x / per_group, first_m = grp * GROUP;
+  const int gsize = min(tiles_m - first_m, GROUP);
+  const int local = blockIdx.x - grp * per_group;
+  const int tm = first_m + local % gsize, tn = local / gsize;
   const int m0 = tm * BM, n0 = tn * BN;
   if (p.sym && m0 + BM - 1 < n0) return;  // tile entirely above the diagonal
 
@@ -348,7 +357,7 @@ kf_status launch(cudaStream_t s, const GemmParams<TE>& g, const TcScratch& sc, i
     KF_TRY(make_map(&maps.b[i], b_is_a ? sc.a[i] : sc.b[i], g.N, ldk, ldk, BN));
   }
   KF_CUDA_TRY(smem_limit_per_device((const void*)tc_gemm_kernel<BN, S, TE>, (int)C::SMEM));
-  dim3 grid((unsigned)ceil_div(g.N, BN), (unsigned)ceil_div(g.M, BM));
+  const dim3 grid((unsigned)(ceil_div(g.N, BN) * ceil_div(g.M, BM)));
   const int num_k_tiles = (int)(ldk / BK);
   if (g_tc_timer) g_tc_timer->before(s);
   tc_gemm_kernel<BN, S, TE><<<grid, NUM_THREADS, C::SMEM, s>>>(maps, g, num_k_tiles, g_tc_wait_ns.load());
