@@ -215,6 +215,20 @@ kf_status kf_plan_profile_read(kf_plan_t p, int32_t cls, int64_t* launches,
 /* Number of kernels this plan has launched since creation (all classes). */
 int64_t kf_plan_launch_count(kf_plan_t p);
 
+/* Device-memory arena for plans (a runtime facility of the library; the paper
+ * has no counterpart).  kf_arena_reserve allocates `bytes` once on the current
+ * device; from then on kf_plan takes its buffers from that reservation
+ * (first fit, 256-byte aligned, falling back to cudaMalloc when the arena is
+ * full) and kf_plan_destroy returns them, so a server that creates and
+ * destroys a plan per request makes no cudaMalloc / cudaFree calls, whose
+ * device-wide synchronisation would stall the other requests' streams.
+ * Thread-safe.  KF_ERR_STATE if an arena is already reserved.
+ * kf_arena_release frees it (KF_ERR_STATE while plans still hold blocks).
+ * kf_arena_stats: reserved bytes, bytes held by plans, largest free block. */
+kf_status kf_arena_reserve(uint64_t bytes);
+kf_status kf_arena_release(void);
+kf_status kf_arena_stats(uint64_t* reserved, uint64_t* in_use, uint64_t* largest_free);
+
 void kf_plan_destroy(kf_plan_t p);
 const char* kf_strerror(kf_status s);
 

@@ -34,10 +34,11 @@ kf_status kfx_gemm(int32_t dtype, int32_t transB, int32_t sym, int64_t M, int64_
  * slice products whose levels sum to less than `levels` are accumulated
  * exactly and summed in 64-bit integers, so element (i, j) is within about
  * 2^(5 - 8 levels) K max|A[i,:]| max|B[j,:]| of the exact product (2^-51 for
- * levels = 7, float64 class; 2^-35 for levels = 5).
+ * levels = 7, float64 class; 2^-35 for levels = 5).  A row of A or B holding an
+ * infinity or NaN gives a NaN row or column of C.
  *   A: M x K, B: N x K (row-major, leading dimensions lda, ldb), float64, or
  *      float32 when a_f32 / b_f32 is set.  C: M x N float64 (in/out when
- *      beta != 0).  K <= 2^20.  levels: 5 or 7.
+ *      beta != 0).  K <= 2^20.  levels: 4 to 7.
  * Allocates its slice buffers (about 2 levels (M + N) K bytes) for the call.
  * Returns KF_ERR_ARG on bad sizes, KF_ERR_UNSUPPORTED without tcgen05. */
 kf_status kfx_gemm_exact(int32_t levels, int64_t M, int64_t N, int64_t K, double alpha, const void* A, int64_t lda,

@@ -62,6 +62,9 @@ _SIGS = {
     "kf_plan_profile_read": (ctypes.c_int, [_P, _I32, ctypes.POINTER(_I64), ctypes.POINTER(_D)]),
     "kf_plan_launch_count": (_I64, [_P]),
     "kf_plan_destroy": (None, [_P]),
+    "kf_arena_reserve": (ctypes.c_int, [ctypes.c_uint64]),
+    "kf_arena_release": (ctypes.c_int, []),
+    "kf_arena_stats": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint64)] * 3),
     "kf_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "kfx_gemm": (ctypes.c_int, [_I32, _I32, _I32, _I64, _I64, _I64, _D, _P, _I64, _P, _I64, _D, _P, _I64, _P]),
     "kfx_gemm_exact": (ctypes.c_int, [_I32, _I64, _I64, _I64, _D, _P, _I64, _I32, _P, _I64, _I32, _D, _D, _P, _I64,
@@ -206,6 +209,20 @@ def kf_solve_host(plan, F, F_rowptr, F_col, Q, H, R, Y, x0, P0, x_filt, diagP_fi
                              _hp(P0), _hp(x_filt), _hp(diagP_filt), _hp(x_smooth), _hp(diagP_smooth),
                              ctypes.byref(fs))
     _check(st, "kf_solve_host", fs.value)
+
+
+def kf_arena_reserve(nbytes: int):
+    _check(lib().kf_arena_reserve(int(nbytes)), "kf_arena_reserve")
+
+
+def kf_arena_release():
+    _check(lib().kf_arena_release(), "kf_arena_release")
+
+
+def kf_arena_stats():
+    r, u, f = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+    _check(lib().kf_arena_stats(ctypes.byref(r), ctypes.byref(u), ctypes.byref(f)), "kf_arena_stats")
+    return r.value, u.value, f.value
 
 
 def kf_plan_profile(plan, enable: bool):

@@ -87,7 +87,7 @@ kf_status kfx_gemm_exact(int32_t levels, int64_t M, int64_t N, int64_t K, double
                          int32_t a_f32, const void* B, int64_t ldb, int32_t b_f32, double beta, double delta, double* C,
                          int64_t ldc, void* stream) {
   if (M < 1 || N < 1 || K < 1 || M > INT32_MAX || N > INT32_MAX || K > (1 << 20)) return KF_ERR_ARG;
-  if (!A || !B || !C || lda < K || ldb < K || ldc < N || (levels != 5 && levels != 7)) return KF_ERR_ARG;
+  if (!A || !B || !C || lda < K || ldb < K || ldc < N || levels < 4 || levels > 7) return KF_ERR_ARG;
   if (!tc_available()) return KF_ERR_UNSUPPORTED;
   cudaStream_t s = (cudaStream_t)stream;
   std::vector<void*> mem;

@@ -1,9 +1,10 @@
 // Exact-slice (Ozaki-scheme) products on the 5th-generation tensor cores.
 //
 // Slicing (oz_slice_kernel): one CTA per row finds the row's largest
-// magnitude, takes its binary exponent e (max < 2^e) and writes the integer
-// slices q_p = rint(v_p), v_0 = x 2^(7-e), v_{p+1} = 256 (v_p - q_p), all exact
-// in float64, as bf16 planes.
+// magnitude, takes its binary exponent e (max < 2^e), rounds each element to
+// the integer X_int = RNE(x 2^(7 + 8(S-1) - e)) and writes its signed base-256
+// digits (|q_p| <= 128) as bf16 planes, in integer arithmetic on the bits of
+// x (the float64 units of this GPU would make float64 slicing the slow part).
 //
 // Product (oz_gemm_kernel): one 128 x 64 output tile per CTA, 18 warps.
 //   warp 0  one lane issues the TMA loads (64-byte swizzle) of all slices of a
@@ -30,25 +31,33 @@ namespace {
 
 constexpr int OZ_BM = 128;      // output rows per CTA (TMEM lanes)
 constexpr int OZ_BN = 64;       // output columns per CTA (TMEM columns per level)
-constexpr int OZ_BK = 32;       // k per stage: one 64-byte swizzle row of bf16
-constexpr int OZ_CK = 4;        // k-slices per exact chunk (128 values of k)
+constexpr int OZ_KC = 128;      // values of k per exact chunk
 constexpr int OZ_EPI_WARPS = 16;  // 4 TMEM lane quadrants x 4 column quarters of 16
 constexpr int OZ_THREADS = 32 * (2 + OZ_EPI_WARPS);
 constexpr int OZ_GROUP = 8;     // row tiles per rasterisation group (operand reuse in L2)
 constexpr int OZ_ROW_PAD = 128;
+constexpr int kOzBK = 16;       // k per pipeline stage of the launched kernels
+constexpr int kOzBadRow = 0x7fffffff;  // exponent marking a row that holds an infinity or NaN
 
-template <int LV>
+// LV slice levels; BK values of k per pipeline stage, one swizzled row of bf16 (16: 32-byte
+// swizzle, 32: 64-byte swizzle): smaller stages give a deeper pipeline for the same shared memory.
+template <int LV, int BK>
 struct OzCfg {
-  static constexpr int A_BYTES = OZ_BM * OZ_BK * 2;
-  static constexpr int B_BYTES = OZ_BN * OZ_BK * 2;
+  static_assert(BK == 16 || BK == 32, "one 32- or 64-byte swizzle row per stage");
+  static constexpr int SWZ = BK * 2;                         // swizzle width in bytes
+  static constexpr uint32_t LAYOUT = BK == 16 ? kLayoutSw32 : kLayoutSw64;  // descriptor swizzle mode
+  static constexpr uint32_t SBO = 8 * SWZ;                   // bytes between 8-row groups
+  static constexpr int CK = OZ_KC / BK;                      // stages per exact chunk
+  static constexpr int A_BYTES = OZ_BM * BK * 2;
+  static constexpr int B_BYTES = OZ_BN * BK * 2;
   static constexpr int STAGE_BYTES = LV * (A_BYTES + B_BYTES);
-  static constexpr int FIT = (200 * 1024) / STAGE_BYTES;
-  static constexpr int STAGES = FIT > 4 ? 4 : FIT;
+  static constexpr int FIT = (210 * 1024) / STAGE_BYTES;
+  static constexpr int STAGES = FIT > 8 ? 8 : FIT;
   static_assert(STAGES >= 2, "double-buffered pipeline");
   static_assert(LV * OZ_BN <= 512, "one TMEM accumulator per level");
   // a level has at most LV slice pairs whose products are below 2^14 in magnitude, so one
-  // chunk of OZ_CK * OZ_BK values of k sums to an integer below 2^24: exact in float32
-  static_assert(LV * OZ_CK * OZ_BK * 16384 <= (1 << 24), "exact chunk");
+  // chunk of OZ_KC values of k sums to an integer below 2^24: exact in float32
+  static_assert(LV * OZ_KC * 16384 <= (1 << 24), "exact chunk");
   static_assert(2 * STAGES + 2 * LV + 1 <= 28, "barriers fit their 256 bytes");
   static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
   // instruction descriptor: D = f32, A = B = bf16, both K-major, N >> 3, M >> 4
@@ -94,7 +103,7 @@ __device__ __forceinline__ void oz_apply(const OzEpilogue& e, int gi, int gj, do
 }
 
 struct OzArgs {
-  int M, N, nk;                  // nk = k-slices of OZ_BK this CTA sums (its split's share)
+  int M, N, nk;                  // nk = k-slices of BK (all of K)
   int kt_per_split;              // k-slices per split (blockIdx.y)
   double* partials;              // splits > 1: raw sums, split s at partials + s M N (ld N)
   int a_rows_pad, b_rows_pad;    // plane p starts at row p * rows_pad of its map
@@ -104,48 +113,126 @@ struct OzArgs {
   uint64_t wait_ns;
 };
 
+// Sign, integer mantissa and binary exponent of x (x = sign mant 2^exp2), read from its bits;
+// false for an infinity or NaN.
+__device__ __forceinline__ bool decompose(double x, long long& mant, int& exp2, bool& neg) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)((b >> 52) & 0x7FF);
+  neg = (b >> 63) != 0;
+  mant = (long long)(b & 0xFFFFFFFFFFFFFull) | (E ? (1ll << 52) : 0ll);
+  exp2 = (E ? E : 1) - 1075;
+  return E != 0x7FF;
+}
+__device__ __forceinline__ bool decompose(float x, long long& mant, int& exp2, bool& neg) {
+  const unsigned b = __float_as_uint(x);
+  const int E = (int)((b >> 23) & 0xFF);
+  neg = (b >> 31) != 0;
+  mant = (long long)(b & 0x7FFFFFu) | (E ? (1ll << 23) : 0ll);
+  exp2 = (E ? E : 1) - 150;
+  return E != 0xFF;
+}
+
+// Magnitude bits of x as an unsigned integer: ordered like |x| for finite values, and above
+// every finite value for infinities and NaNs.
+__device__ __forceinline__ unsigned long long mag_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+__device__ __forceinline__ unsigned long long mag_bits(float x) {
+  return ((unsigned long long)(__float_as_uint(x) & 0x7FFFFFFFu)) << 29;  // same order as a double's bits
+}
+__device__ __forceinline__ int frexp_exponent(unsigned long long mag, bool f32) {
+  const double v = f32 ? (double)__uint_as_float((unsigned)(mag >> 29)) : __longlong_as_double((long long)mag);
+  int e = 0;
+  if (v > 0.0) frexp(v, &e);
+  return e;
+}
+
+// x 2^shift rounded to the nearest integer, ties to even (exact integer arithmetic).
+__device__ __forceinline__ long long fixed_rne(long long mant, int exp2, bool neg, int shift) {
+  const int total = exp2 + shift;
+  long long r;
+  if (total >= 0) {
+    r = total >= 11 ? 0 : mant << total;  // |x| 2^shift < 2^63: total >= 11 only for mant = 0
+  } else {
+    const int sh = -total;
+    if (sh >= 63) {
+      r = 0;
+    } else {
+      long long q = mant >> sh;
+      const long long rem = mant & ((1ll << sh) - 1), half = 1ll << (sh - 1);
+      if (rem > half || (rem == half && (q & 1))) ++q;
+      r = q;
+    }
+  }
+  return neg ? -r : r;
+}
+
+// Slices of one row: X[r][k] = 2^(e - 7 - 8(S-1)) X_int with X_int = RNE(X[r][k] 2^(7 + 8(S-1) - e)),
+// written in signed base-256 digits q_0 .. q_{S-1} (each rounded to nearest, ties to even, so
+// |q_p| <= 128), all in integer arithmetic.
 template <typename T>
 __global__ void __launch_bounds__(256) oz_slice_kernel(const T* X, int64_t ld, int64_t rows, int64_t cols, int S,
                                                        __nv_bfloat16* planes, int64_t rows_pad, int64_t ldk,
                                                        int* exps) {
-  __shared__ double red[8];
+  __shared__ unsigned long long red[8];
   const int64_t r = blockIdx.x;
   const T* row = X + r * ld;
-  double mx = 0.0;
+  unsigned long long mx = 0;
   if (r < rows)
-    for (int64_t k = threadIdx.x; k < cols; k += blockDim.x) mx = fmax(mx, fabs((double)row[k]));
+    for (int64_t k = threadIdx.x; k < cols; k += blockDim.x) {
+      const unsigned long long v = mag_bits(row[k]);
+      mx = v > mx ? v : mx;
+    }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long v = __shfl_xor_sync(0xffffffffu, mx, o);
+    mx = v > mx ? v : mx;
+  }
   if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = mx;
   __syncthreads();
   mx = red[0];
-  for (int w = 1; w < (int)blockDim.x / 32; ++w) mx = fmax(mx, red[w]);
-  int e = 0;
-  if (mx > 0.0 && isfinite(mx)) frexp(mx, &e);  // mx = f 2^e, 0.5 <= f < 1
-  if (threadIdx.x == 0) exps[r] = e;
+  for (int w = 1; w < (int)blockDim.x / 32; ++w) mx = red[w] > mx ? red[w] : mx;
+  const bool row_bad = mx >= 0x7FF0000000000000ull;  // an infinity or NaN: zero slices, marked exponent
+  const int e = row_bad ? 0 : frexp_exponent(mx, sizeof(T) == 4);  // max |X[r]| < 2^e
+  if (threadIdx.x == 0) exps[r] = row_bad ? kOzBadRow : e;
+  const int shift = 7 + 8 * (S - 1) - e;
   const int64_t pstride = rows_pad * ldk;
   for (int64_t k0 = threadIdx.x * 8; k0 < ldk; k0 += (int64_t)blockDim.x * 8) {
-    double v[8];
+    long long xi[8];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) v[i] = (r < rows && k0 + i < cols) ? scalbn((double)row[k0 + i], 7 - e) : 0.0;
+    for (int i = 0; i < 8; ++i) {
+      xi[i] = 0;
+      if (r < rows && k0 + i < cols && !row_bad) {
+        long long mant;
+        int exp2;
+        bool neg;
+        decompose(row[k0 + i], mant, exp2, neg);
+        xi[i] = fixed_rne(mant, exp2, neg, shift);
+      }
+    }
     for (int p = 0; p < S; ++p) {
+      const int sp = 8 * (S - 1 - p);
       uint32_t w[4];
 #pragma unroll
       for (int i = 0; i < 8; i += 2) {
-        const double q0 = rint(v[i]), q1 = rint(v[i + 1]);  // |q| <= 128: exact in bf16
-        w[i / 2] = (uint32_t)__bfloat16_as_ushort(__double2bfloat16(q0)) |
-                   ((uint32_t)__bfloat16_as_ushort(__double2bfloat16(q1)) << 16);
-        v[i] = (v[i] - q0) * 256.0;
-        v[i + 1] = (v[i + 1] - q1) * 256.0;
+        __nv_bfloat16 h[2];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          long long q = xi[i + j];
+          if (sp > 0) q = (q + (1ll << (sp - 1)) - 1 + ((q >> sp) & 1)) >> sp;
+          xi[i + j] -= q << sp;
+          h[j] = __float2bfloat16_rn((float)q);
+        }
+        w[i / 2] = (uint32_t)__bfloat16_as_ushort(h[0]) | ((uint32_t)__bfloat16_as_ushort(h[1]) << 16);
       }
       *reinterpret_cast<uint4*>(planes + p * pstride + r * ldk + k0) = make_uint4(w[0], w[1], w[2], w[3]);
     }
   }
 }
 
-template <int LV>
+template <int LV, int BK>
 __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_constant__ OzMaps maps, const OzArgs a) {
-  using C = OzCfg<LV>;
+  using C = OzCfg<LV, BK>;
   extern __shared__ uint8_t smem_raw[];
   // grouped rasterisation: OZ_GROUP row tiles sweep the column tiles together
   const int tiles_m = (a.M + OZ_BM - 1) / OZ_BM, tiles_n = (a.N + OZ_BN - 1) / OZ_BN;
@@ -198,14 +285,14 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
   const bool skip = *skip_flag != 0 || nk <= 0;
-  const int nchunks = (nk + OZ_CK - 1) / OZ_CK;
+  const int nchunks = (nk + C::CK - 1) / C::CK;
   bool mma_issued = false;
 
   if (skip) {
     // an earlier kernel failed: do nothing but release TMEM below
   } else if (warp == 0 && lane == 0) {
     // ---------------- TMA producer
-    int last_round[4] = {-1, -1, -1, -1};
+    int last_round[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
     for (int it = 0; it < nk; ++it) {
       const int s = it % C::STAGES;
       const uint32_t ph = (uint32_t)(it / C::STAGES) & 1u;
@@ -216,7 +303,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
       }
       const uint32_t st = base + s * C::STAGE_BYTES;
       mbar_expect_tx(full_bar(s), C::STAGE_BYTES);
-      const int x = (kt0 + it) * OZ_BK;
+      const int x = (kt0 + it) * BK;
 #pragma unroll
       for (int p = 0; p < LV; ++p) tma_load_2d(st + p * C::A_BYTES, &maps.a, x, p * a.a_rows_pad + m0, full_bar(s));
 #pragma unroll
@@ -241,9 +328,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t st = base + s * C::STAGE_BYTES;
-      const int c = it / OZ_CK;
-      const bool first = (it % OZ_CK) == 0;
-      const bool last = (it % OZ_CK) == OZ_CK - 1 || it == nk - 1;
+      const int c = it / C::CK;
+      const bool first = (it % C::CK) == 0;
+      const bool last = (it % C::CK) == C::CK - 1 || it == nk - 1;
 #pragma unroll
       for (int l = 0; l < LV; ++l) {
         if (first && c > 0 && !mbar_wait(drained_bar(l), (uint32_t)(c - 1) & 1u, abort_flag, a.wait_ns)) {
@@ -258,10 +345,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
         for (int pa = 0; pa <= l; ++pa) {
           const int pb = l - pa;
 #pragma unroll
-          for (int kk = 0; kk < OZ_BK / 16; ++kk) {
+          for (int kk = 0; kk < BK / 16; ++kk) {
             const uint32_t acc = (first && pa == 0 && kk == 0) ? 0u : 1u;
-            mma_bf16(dacc, smem_desc_sw(st + pa * C::A_BYTES + kk * 32, 512, kLayoutSw64),
-                     smem_desc_sw(st + LV * C::A_BYTES + pb * C::B_BYTES + kk * 32, 512, kLayoutSw64), C::IDESC,
+            mma_bf16(dacc, smem_desc_sw(st + pa * C::A_BYTES + kk * 32, C::SBO, C::LAYOUT),
+                     smem_desc_sw(st + LV * C::A_BYTES + pb * C::B_BYTES + kk * 32, C::SBO, C::LAYOUT), C::IDESC,
                      acc);
           }
         }
@@ -312,8 +399,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
       for (int j = 0; j < 16; ++j) {
         const int gj = n0 + h * 16 + j;
         if (gj < a.N && !(a.e.sym && gj > gi)) {
-          const int sc = ei + a.eb[gj] - 14;
-          const double cval = scalbn((double)hi[j], sc - 16) + scalbn((double)lo[j], sc - 8 * (LV - 1));
+          const int ej = a.eb[gj];
+          const int sc = ei + ej - 14;
+          const double cval = (ei == kOzBadRow || ej == kOzBadRow)
+                                  ? __longlong_as_double(0x7ff8000000000000ll)  // a non-finite operand row
+                                  : scalbn((double)hi[j], sc - 16) + scalbn((double)lo[j], sc - 8 * (LV - 1));
           if (part)
             part[(int64_t)gi * a.N + gj] = cval;
           else
@@ -348,18 +438,19 @@ __global__ void oz_reduce_kernel(int M, int N, int splits, const double* partial
   }
 }
 
-template <int LV>
+template <int LV, int BK>
 kf_status launch_oz(cudaStream_t s, const OzSlices& A, const OzSlices& B, int M, int N, int K, const OzEpilogue& e,
                     int splits, double* partials) {
-  using C = OzCfg<LV>;
+  using C = OzCfg<LV, BK>;
   OzMaps maps;
-  KF_TRY(tma_map_bf16(&maps.a, A.planes, (int64_t)A.S * A.rows_pad, A.ldk, A.ldk, OZ_BK, OZ_BM, 64));
-  KF_TRY(tma_map_bf16(&maps.b, B.planes, (int64_t)B.S * B.rows_pad, B.ldk, B.ldk, OZ_BK, OZ_BN, 64));
+  KF_TRY(tma_map_bf16(&maps.a, A.planes, (int64_t)A.S * A.rows_pad, A.ldk, A.ldk, BK, OZ_BM, C::SWZ));
+  KF_TRY(tma_map_bf16(&maps.b, B.planes, (int64_t)B.S * B.rows_pad, B.ldk, B.ldk, BK, OZ_BN, C::SWZ));
   OzArgs a;
   a.M = M;
   a.N = N;
-  a.nk = (int)ceil_div(K, OZ_BK);
-  a.kt_per_split = (int)ceil_div(a.nk, splits);
+  a.nk = (int)ceil_div(K, BK);
+  // whole exact chunks per split, so chunk boundaries do not depend on the split
+  a.kt_per_split = (int)(ceil_div(ceil_div(K, OZ_KC), splits) * C::CK);
   a.partials = splits > 1 ? partials : nullptr;
   a.a_rows_pad = (int)A.rows_pad;
   a.b_rows_pad = (int)B.rows_pad;
@@ -367,10 +458,10 @@ kf_status launch_oz(cudaStream_t s, const OzSlices& A, const OzSlices& B, int M,
   a.eb = B.exps;
   a.e = e;
   a.wait_ns = g_tc_wait_ns.load();
-  KF_CUDA_TRY(smem_limit_per_device((const void*)oz_gemm_kernel<LV>, (int)C::SMEM));
+  KF_CUDA_TRY(smem_limit_per_device((const void*)oz_gemm_kernel<LV, BK>, (int)C::SMEM));
   const int64_t tiles = ceil_div(M, OZ_BM) * ceil_div(N, OZ_BN);
   if (g_tc_timer) g_tc_timer->before(s);
-  oz_gemm_kernel<LV><<<dim3((unsigned)tiles, (unsigned)splits), OZ_THREADS, C::SMEM, s>>>(maps, a);
+  oz_gemm_kernel<LV, BK><<<dim3((unsigned)tiles, (unsigned)splits), OZ_THREADS, C::SMEM, s>>>(maps, a);
   if (g_tc_timer) g_tc_timer->after(s);
   note_launch();
   KF_TRY(launch_check("oz_gemm"));
@@ -423,12 +514,16 @@ kf_status oz_gemm(cudaStream_t s, const OzSlices& A, const OzSlices& B, int M, i
   if (M > A.rows || N > B.rows || K > A.ldk || K > B.ldk) return KF_ERR_ARG;
   if (A.filled < levels || B.filled < levels || (e.sym && M != N)) return KF_ERR_ARG;
   if (splits < 1 || splits > 64 || (splits > 1 && !partials)) return KF_ERR_ARG;
-  // every split gets at least one k-slice
-  splits = (int)std::min<int64_t>(splits, ceil_div(K, OZ_BK));
-  const int kps = (int)ceil_div(ceil_div(K, OZ_BK), splits);
-  splits = (int)ceil_div(ceil_div(K, OZ_BK), kps);
-  if (levels == 5) return launch_oz<5>(s, A, B, M, N, K, e, splits, partials);
-  if (levels == 7) return launch_oz<7>(s, A, B, M, N, K, e, splits, partials);
+  // whole exact chunks per split, every split non-empty
+  const int64_t chunks = ceil_div(K, OZ_KC);
+  splits = (int)std::min<int64_t>(splits, chunks);
+  splits = (int)ceil_div(chunks, ceil_div(chunks, splits));
+  switch (levels) {
+    case 4: return launch_oz<4, kOzBK>(s, A, B, M, N, K, e, splits, partials);
+    case 5: return launch_oz<5, kOzBK>(s, A, B, M, N, K, e, splits, partials);
+    case 6: return launch_oz<6, kOzBK>(s, A, B, M, N, K, e, splits, partials);
+    case 7: return launch_oz<7, kOzBK>(s, A, B, M, N, K, e, splits, partials);
+  }
   return KF_ERR_ARG;
 }
 

@@ -6,9 +6,11 @@
 // and Its Accurate and Reproducible Versions").
 //
 // Row r of an operand X (rows x K) is written as
-//     X[r][k] = 2^(e_r - 7) * sum_{p < S} 2^(-8p) q_p[r][k]
+//     X[r][k] ~= 2^(e_r - 7) * sum_{p < S} 2^(-8p) q_p[r][k]
 // with e_r the exponent of the row's largest magnitude (max |X[r][:]| < 2^e_r)
-// and integer slices q_p in [-128, 128], each exact in bf16.  A product of two
+// and integer slices q_p in [-128, 128], each exact in bf16: the signed
+// base-256 digits (each rounded to nearest, ties to even) of X[r][k] rounded
+// to the grid 2^(e_r - 7 - 8(S-1)).  A product of two
 // slices is an integer below 2^14, so the sum over k of the products of one
 // slice level l = p_A + p_B is an exact integer as long as it stays below 2^24:
 // the tensor cores' float32 accumulation (which truncates) then loses nothing.
@@ -78,7 +80,7 @@ struct OzEpilogue {
 };
 
 // C = A B^T for A (M x K) and B (N x K) given by their slices, keeping the
-// slice levels l < levels (5 or 7; both operands need at least `levels`
+// slice levels l < levels (4 to 7; both operands need at least `levels`
 // slices).  K <= 2^20.  splits > 1 divides K among that many CTAs per output
 // tile, whose float64 partial sums (splits x M x N doubles at `partials`) are
 // added in a fixed order by a second kernel that applies the epilogue.

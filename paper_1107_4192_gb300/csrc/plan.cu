@@ -17,6 +17,7 @@
 
 #include <vector>
 
+#include "arena.cuh"
 #include "ops.cuh"
 #include "solve_tc.cuh"
 #include "tc_gemm.cuh"
@@ -80,7 +81,7 @@ struct kf_plan_s {
   double *F = nullptr, *Q = nullptr, *H = nullptr, *R = nullptr;
   int64_t *Frp = nullptr, *Fcol = nullptr;
   int* status = nullptr;
-  int* status_h = nullptr;
+  int status_h[ST_WORDS] = {0, 0, 0, 0};  // read after a stream synchronisation
   bool filtered = false;
   // staging for kf_solve_host (allocated on first use)
   double *hY = nullptr, *hx0 = nullptr, *hP0 = nullptr, *hQ = nullptr, *hH = nullptr, *hR = nullptr,
@@ -205,7 +206,8 @@ template <typename X>
 kf_status dalloc(kf_plan_s* p, X** out, size_t bytes) {
   void* ptr = nullptr;
   if (bytes == 0) bytes = 16;
-  cudaError_t e = cudaMalloc(&ptr, bytes);
+  ptr = arena_alloc(bytes);  // the reserved arena first (no device-wide synchronisation)
+  cudaError_t e = ptr ? cudaSuccess : cudaMalloc(&ptr, bytes);
   if (e != cudaSuccess) {
     fprintf(stderr, "kfmeg: cudaMalloc(%zu) failed: %s\n", bytes, cudaGetErrorString(e));
     cudaGetLastError();
@@ -1057,7 +1059,6 @@ kf_status kf_plan(kf_plan_t* out, const kf_desc* d) {
   if (st == KF_OK && p->bulk == BULK_BF16X3) st = tc_scratch_alloc(p->tc, std::max(N, m), std::max(ldN, 2 * ldm), [&](void** ptr, size_t bytes) {
     return dalloc(p, (char**)ptr, bytes);
   });
-  if (st == KF_OK && cudaMallocHost(&p->status_h, ST_WORDS * sizeof(int)) != cudaSuccess) st = KF_ERR_CUDA;
   if (st == KF_OK && cudaStreamSynchronize(p->s) != cudaSuccess) st = KF_ERR_CUDA;
   if (st != KF_OK) {
     kf_plan_destroy(p);
@@ -1200,13 +1201,17 @@ void kf_plan_destroy(kf_plan_t p) {
   if (p->s) cudaStreamSynchronize(p->s);
   if (p->chol_graph) cudaGraphExecDestroy(p->chol_graph);
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
-  for (void* a : p->allocs) cudaFree(a);
+  for (void* a : p->allocs) {
+    if (arena_owns(a))
+      arena_free(a);
+    else
+      cudaFree(a);
+  }
   for (auto& mk : p->marks) {
     cudaEventDestroy(mk.a);
     cudaEventDestroy(mk.b);
   }
   for (auto e : p->pool) cudaEventDestroy(e);
-  if (p->status_h) cudaFreeHost(p->status_h);
   delete p;
 }
 

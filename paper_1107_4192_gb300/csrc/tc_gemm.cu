@@ -417,7 +417,8 @@ kf_status tma_map_bf16(CUtensorMap* map, const void* ptr, int64_t rows, int64_t 
                        int box_rows, int swizzle_bytes) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return KF_ERR_UNSUPPORTED;
-  if (box_cols * 2 != swizzle_bytes || (swizzle_bytes != 64 && swizzle_bytes != 128)) return KF_ERR_ARG;
+  if (box_cols * 2 != swizzle_bytes || (swizzle_bytes != 32 && swizzle_bytes != 64 && swizzle_bytes != 128))
+    return KF_ERR_ARG;
   if ((reinterpret_cast<uintptr_t>(ptr) & 15) || ((ld * 2) & 15) || cols % box_cols) return KF_ERR_ARG;
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
@@ -425,7 +426,9 @@ kf_status tma_map_bf16(CUtensorMap* map, const void* ptr, int64_t rows, int64_t 
   cuuint32_t estr[2] = {1, 1};
   CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, estr,
                    CU_TENSOR_MAP_INTERLEAVE_NONE,
-                   swizzle_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
+                   swizzle_bytes == 32   ? CU_TENSOR_MAP_SWIZZLE_32B
+                   : swizzle_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                         : CU_TENSOR_MAP_SWIZZLE_128B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? KF_OK : KF_ERR_CUDA;
 }

@@ -39,7 +39,7 @@ bool tc_available();
 
 // 2-D TMA map of a bf16 matrix (rows x cols, leading dimension ld elements,
 // 16-byte aligned rows) with a box of box_cols x box_rows and the given
-// swizzle (64 or 128 bytes; the box row must be that wide).
+// swizzle (32, 64 or 128 bytes; the box row must be that wide).
 kf_status tma_map_bf16(CUtensorMap* map, const void* ptr, int64_t rows, int64_t cols, int64_t ld, int box_cols,
                        int box_rows, int swizzle_bytes);
 

@@ -88,8 +88,8 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
 // rows: start address >> 4 (bits 0-13), LBO (bits 16-29, unused for swizzled
 // K-major tiles whose MMA K extent fits in one swizzle row), SBO = byte
 // stride between 8-row groups (bits 32-45), fixed version field 0b001 (bits
-// 46-48), swizzle mode (bits 61-63: 2 = 128-byte, 4 = 64-byte).
-constexpr uint32_t kLayoutSw128 = 2, kLayoutSw64 = 4;
+// 46-48), swizzle mode (bits 61-63: 2 = 128-byte, 4 = 64-byte, 6 = 32-byte).
+constexpr uint32_t kLayoutSw128 = 2, kLayoutSw64 = 4, kLayoutSw32 = 6;
 __device__ __forceinline__ uint64_t smem_desc_sw(uint32_t addr, uint32_t sbo_bytes, uint32_t layout) {
   uint64_t d = 0;
   d |= (uint64_t)((addr & 0x3FFFFu) >> 4);

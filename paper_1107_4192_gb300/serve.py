@@ -18,6 +18,11 @@ Every epoch's computation is independent of the others (own plan, own
 stream, deterministic kernels), so a result is bitwise the same alone and in
 the mix.
 
+Plans take their device memory from an arena the server reserves once
+(kf_arena_reserve, the size of the budget): creating and destroying a plan
+per request then makes no cudaMalloc / cudaFree call, whose device-wide
+synchronisation would stall the other requests' streams.
+
 Only marshalling and scheduling happen here; all arithmetic runs in the
 library's CUDA kernels.
 """
@@ -96,11 +101,12 @@ class Server:
     """Admits requests as slots and memory free up; runs each on its own stream."""
 
     def __init__(self, budget_bytes: int = 160 * 10 ** 9, max_slots: int = 4, keep_outputs: bool = False,
-                 device: str = "cuda"):
+                 device: str = "cuda", use_arena: bool = True):
         self.budget = int(budget_bytes)
         self.max_slots = max_slots
         self.keep_outputs = keep_outputs
         self.device = device
+        self.use_arena = use_arena
         self._lock = threading.Lock()
         self._cv = threading.Condition(self._lock)
         self._in_use = 0
@@ -156,6 +162,14 @@ class Server:
         results = {r.rid: Result(r.rid, r.problem.N, r.problem.m, r.problem.T, r.arrival_s * time_scale)
                    for r in reqs}
         threads = []
+        arena = False
+        if self.use_arena:
+            # plans sub-allocate from one reservation; fall back to cudaMalloc if it cannot be made
+            try:
+                B.kf_arena_reserve(self.budget)
+                arena = True
+            except B.KfError:
+                arena = False
         t0 = time.perf_counter()
         pending: List[Request] = []
         i = 0
@@ -193,6 +207,8 @@ class Server:
                 self._cv.wait(timeout=timeout)
         for th in threads:
             th.join()
+        if arena:
+            B.kf_arena_release()
         return [results[r.rid] for r in reqs]
 
 

@@ -31,18 +31,26 @@ def _lib():
     B.lib()
 
 
+def rne_shift(a, s):
+    """a / 2^s rounded to nearest, ties to even, for int64 arrays."""
+    return (a + (1 << (s - 1)) - 1 + ((a >> s) & 1)) >> s
+
+
 def slices_ref(X, S):
     """Row exponents e (max |X[r]| < 2^e) and integer slices q_p with
-    X[r] = 2^(e_r - 7) sum_p 2^(-8p) q_p[r] (up to the last slice's truncation)."""
+    X[r] ~= 2^(e_r - 7) sum_p 2^(-8p) q_p[r]: the signed base-256 digits (rounded to nearest,
+    ties to even) of X rounded to the grid 2^(e_r - 7 - 8(S - 1))."""
     X = np.asarray(X, np.float64)
     mx = np.abs(X).max(axis=1)
     e = np.where(mx > 0, np.frexp(mx)[1], 0).astype(np.int64)
-    v = np.ldexp(X, (7 - e)[:, None])
+    Xi = np.rint(np.ldexp(X, (7 + 8 * (S - 1) - e)[:, None])).astype(np.int64)
     qs = []
-    for _ in range(S):
-        q = np.rint(v)
-        qs.append(q.astype(np.int64))
-        v = (v - q) * 256.0
+    for p in range(S):
+        sp = 8 * (S - 1 - p)
+        q = rne_shift(Xi, sp) if sp > 0 else Xi.copy()
+        assert np.abs(q).max(initial=0) <= 128
+        Xi = Xi - (q << sp)
+        qs.append(q)
     return e, qs
 
 
@@ -62,7 +70,7 @@ def exact_sliced_product(A, Bm, L):
     return out, ea, eb
 
 
-@pytest.mark.parametrize("levels", [5, 7])
+@pytest.mark.parametrize("levels", [4, 5, 6, 7])
 @pytest.mark.parametrize("M,N,K", [(130, 70, 300), (256, 192, 1024), (1, 1, 1), (129, 65, 33)])
 def test_exact_product_matches_the_scheme(levels, M, N, K):
     rng = np.random.default_rng(M + N + K + levels)
@@ -78,7 +86,7 @@ def test_exact_product_matches_the_scheme(levels, M, N, K):
     assert np.all(np.abs(got - ref) <= 2.0 ** -50 * scale * max(1, K) ** 0.0 + 4 * np.spacing(np.abs(ref)))
 
 
-@pytest.mark.parametrize("levels", [5, 7])
+@pytest.mark.parametrize("levels", [4, 5, 6, 7])
 def test_exact_product_accuracy_and_epilogue(levels):
     """Against the true product (extended precision); alpha, beta and the delta on the diagonal."""
     rng = np.random.default_rng(7 + levels)
@@ -151,3 +159,19 @@ def test_refined_inverse_reports_not_pd():
     X = torch.zeros(n, n, dtype=torch.float64, device="cuda")
     st, fi = B.kfx_spd_inverse(2, n, torch.from_numpy(A.astype(np.float32)).cuda(), n, X, n)
     assert st == B.KF_ERR_NOT_PD and fi == 150
+
+
+def test_exact_product_non_finite_rows_give_nan():
+    """A NaN or infinity in a row of A makes that output row NaN (and no other)."""
+    rng = np.random.default_rng(11)
+    M, N, K = 40, 30, 50
+    A = rng.standard_normal((M, K))
+    Bm = rng.standard_normal((N, K))
+    A[3, 7] = np.nan
+    A[9, 0] = np.inf
+    C = torch.zeros(M, N, dtype=torch.float64, device="cuda")
+    B.kfx_gemm_exact(5, M, N, K, 1.0, torch.from_numpy(A).cuda(), K, torch.from_numpy(Bm).cuda(), K, 0.0, 0.0, C, N)
+    got = C.cpu().numpy()
+    bad = np.zeros(M, bool)
+    bad[[3, 9]] = True
+    assert np.all(np.isnan(got[bad])) and np.all(np.isfinite(got[~bad]))

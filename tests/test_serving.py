@@ -100,3 +100,35 @@ def test_mid_size_concurrent_equals_alone(built):
         assert a.status == b.status == "ok", (a.status, b.status)
         for k in a.outputs:
             assert np.array_equal(a.outputs[k], b.outputs[k]), (a.rid, k)
+
+
+@pytest.mark.gpu
+def test_arena_backs_plans_without_allocation(built):
+    """Plans created after kf_arena_reserve take their buffers from the arena (in_use grows by the
+    plan's footprint), return them on destroy (coalesced back to one free block), and compute
+    the same result as a plan from cudaMalloc."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1107_4192_gb300 import solver
+    prob = synth.mesh_problem(324, 40, 6, seed=2)
+    ref = solver.run(prob, prec=B.KF_PREC_MIXED_BF16X3, solve_prec=B.KF_SOLVE_FP32, joseph_every=4)
+    size = 4 * 10 ** 9
+    B.kf_arena_reserve(size)
+    try:
+        r, u, f = B.kf_arena_stats()
+        assert r > 0.99 * size and u == 0 and f == r
+        out = solver.run(prob, prec=B.KF_PREC_MIXED_BF16X3, solve_prec=B.KF_SOLVE_FP32, joseph_every=4)
+        d = solver.upload(prob)
+        plan = solver.Plan.for_inputs(d, prob.N, prob.m, prob.T, prec=B.KF_PREC_MIXED_BF16X3,
+                                      solve_prec=B.KF_SOLVE_FP32, joseph_every=4)
+        _, u1, _ = B.kf_arena_stats()
+        st, w, s, _ = B.kf_plan_footprint(plan.desc)
+        assert u1 >= 0.9 * (w + s)
+        plan.close()
+        r2, u2, f2 = B.kf_arena_stats()
+        assert u2 == 0 and f2 == r2
+    finally:
+        B.kf_arena_release()
+    for k in ref:
+        assert np.array_equal(ref[k], out[k]), k
