@@ -150,6 +150,10 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=12,
                     help="requests of the Poisson serving stream to replay (0 = skip)")
     ap.add_argument("--batch-epochs", type=int, default=64, help="uneven epochs of the batched workload (0 = skip)")
+    ap.add_argument("--config1-prefix", type=int, default=10,
+                    help="time steps of the N=5124 mesh epoch run in float64 and float32 (0 = skip the config 1 leg)")
+    ap.add_argument("--no-config2-mesh", action="store_true",
+                    help="skip the N=8196 mesh-F epoch that runs with checkpoint recomputation under 160 GB")
     return ap.parse_args()
 
 
@@ -415,6 +419,10 @@ def main():
         line["serve"] = serving_sample(args, B, synth)
     if rank == 0 and world == 1 and not args.no_fp64_plain and args.prec != "fp64":
         line["fp64_plain"] = fp64_plain_prefix(prob, B, solver, synth, torch)
+    if rank == 0 and world == 1 and args.config1_prefix > 0:
+        line["config1"] = config1_sample(args, B, solver, synth, torch)
+    if rank == 0 and world == 1 and not args.no_config2_mesh:
+        line["config2_mesh_recompute"] = config2_mesh_sample(args, B, solver, synth, torch)
     if rank == 0 and world == 1:
         line["mne_init"] = mne_init_sample(prob, B, solver, torch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -454,6 +462,64 @@ def batched_sample(args, B, synth):
     summ["epochs_per_s"] = summ["completed"] / summ["wall_s"] if summ["wall_s"] > 0 else 0.0
     summ["sample"] = f"{len(probs)} epochs, 8 concurrent plans on separate streams"
     return summ
+
+
+def _epoch_rate(prob, B, solver, torch, reps=1, **kw):
+    """timesteps/s of filter + smoother over the whole problem (inputs resident), after one warm-up."""
+    d = solver.upload(prob)
+    plan = solver.Plan.for_inputs(d, prob.N, prob.m, prob.T, stream=torch.cuda.current_stream().cuda_stream, **kw)
+    x = torch.empty(prob.T, prob.N, dtype=torch.float64, device="cuda")
+
+    def run():
+        B.kf_filter(plan.handle, d.F, d.F_rowptr, d.F_col, d.Q, d.H, d.R, d.Y, d.x0, d.P0, x)
+        B.fis_smooth(plan.handle, x)
+
+    run()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        run()
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / reps
+    ck = B.kf_plan_footprint(plan.desc)[3]
+    plan.close()
+    return prob.T / dt, dt, ck
+
+
+def config1_sample(args, B, solver, synth, torch):
+    """Config 1 (N = 5124 sources on two icospheres, mesh F, m = 306, T = 200): float64 and float32
+    on the GPU on a T-prefix (the float64 smoother takes ~0.6 s per step at this N), and the mixed
+    path with the float64-accurate tensor-core solve over the whole epoch."""
+    T_pre = args.config1_prefix
+    out = {"workload": "N5124_m306_T200_mesh (config 1)", "unit": "timesteps/s"}
+    pre = synth.config1(T=T_pre)
+    for name, kw in (("fp64", dict(prec=B.KF_PREC_FP64)),
+                     ("fp32", dict(prec=B.KF_PREC_FP32, solve_prec=B.KF_SOLVE_FP64))):
+        r, dt, _ = _epoch_rate(pre, B, solver, torch, **kw)
+        out[f"{name}_prefix"] = {"value": r, "sample": f"T={T_pre} prefix, filter + smoother", "s": dt}
+    full = synth.config1()
+    r, dt, _ = _epoch_rate(full, B, solver, torch, prec=B.KF_PREC_MIXED_BF16X3, solve_prec=B.KF_SOLVE_FP64_TC,
+                           joseph_every=16)
+    out["mixed_fp64tc"] = {"value": r, "sample": "whole T=200 epoch, split-bf16 bulk, float64-accurate solve", "s": dt}
+    return out
+
+
+def config2_mesh_sample(args, B, solver, synth, torch):
+    """Config 2 (ii): N = 8196 with the mesh coupling F = 0.9 I + 0.016 A, m = 306, T = 300, mixed path.
+    The footprint rule of the workload, 2 N^2 T float32 words (predicted and filtered covariances),
+    is 161 GB > 160 GB, so the epoch runs in recompute mode: checkpoints of P_{t|t} every
+    round(sqrt(T)) steps, the other steps recomputed forward during the smoother.  (This plan
+    stores only P_{t|t} and rebuilds P_{t+1|t} = F P F^T + Q from it, so its full store would
+    take half that.)  One whole epoch."""
+    prob = synth.config2(identity_F=False)
+    budget = 160 * 10 ** 9
+    rule = 2 * prob.N * prob.N * prob.T * 4
+    ck = int(round(np.sqrt(prob.T))) if rule > budget else 0
+    solve = {"fp32": B.KF_SOLVE_FP32, "fp64": B.KF_SOLVE_FP64, "fp64tc": B.KF_SOLVE_FP64_TC}[args.solve]
+    r, dt, ck_used = _epoch_rate(prob, B, solver, torch, prec=B.KF_PREC_MIXED_BF16X3, solve_prec=solve,
+                                 joseph_every=16, mem_budget_bytes=budget, checkpoint_every=ck)
+    return {"workload": prob.name, "value": r, "unit": "timesteps/s", "s": dt, "checkpoint_every": ck_used,
+            "footprint_rule_bytes": rule, "budget_bytes": budget, "solve": args.solve}
 
 
 def mne_init_sample(prob, B, solver, torch):

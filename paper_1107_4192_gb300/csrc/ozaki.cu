@@ -152,7 +152,8 @@ __device__ __forceinline__ long long fixed_rne(long long mant, int exp2, bool ne
   const int total = exp2 + shift;
   long long r;
   if (total >= 0) {
-    r = total >= 11 ? 0 : mant << total;  // |x| 2^shift < 2^63: total >= 11 only for mant = 0
+    // |x| 2^shift < 2^(7 + 8(S-1)) <= 2^55 for every element of the row, so the shift cannot overflow
+    r = total >= 63 ? 0 : mant << total;
   } else {
     const int sh = -total;
     if (sh >= 63) {

@@ -104,15 +104,16 @@ def test_checkpoint_recompute_is_bitwise_identical(prec):
             assert np.array_equal(full[k], part[k]), (c, k)
 
 
+@pytest.mark.parametrize("solve", [B.KF_SOLVE_FP32, B.KF_SOLVE_FP64_TC])
 @pytest.mark.parametrize("mesh", [False, True])
 @pytest.mark.parametrize("c", [2, 5])
-def test_mixed_checkpoint_recompute(mesh, c):
+def test_mixed_checkpoint_recompute(mesh, c, solve):
     """Mixed path with only every c-th P_{t|t} kept: the skipped steps are recomputed during the
     smoother from float32 checkpoints (the float64 working covariance restarts from a float32
     value), so results differ from the full store by rounding only; both stay within the mixed
     tolerances of the oracle."""
     prob = synth.mesh_problem(324, 30, 17, seed=8, identity_F=not mesh)
-    kw = dict(prec=B.KF_PREC_MIXED_BF16X3, solve_prec=B.KF_SOLVE_FP32, joseph_every=4)
+    kw = dict(prec=B.KF_PREC_MIXED_BF16X3, solve_prec=solve, joseph_every=4)
     ref = run_oracle(prob)
     full = solver.run(prob, **kw)
     part = solver.run(prob, checkpoint_every=c, **kw)
@@ -146,18 +147,24 @@ def test_dense_F_equals_compressed_rows_fp64():
         assert rel_err_per_step(a[k], b[k]) <= 1e-12, k
 
 
-def test_mixed_long_epoch_T300():
-    """Mixed path over a 300-step epoch (Joseph form every 16 steps, float32 store), the
-    configuration of the N = 8196 benchmark at N = 1024: the split-bf16 error must not build up
-    through the smoother's covariance recursion beyond the mixed tolerances."""
+@pytest.fixture(scope="module")
+def long_epoch():
     prob = synth.mesh_problem(1024, 306, 300, seed=11, identity_F=True)
-    ref = run_oracle(prob)
-    out = solver.run(prob, prec=B.KF_PREC_MIXED_BF16X3, solve_prec=B.KF_SOLVE_FP32, joseph_every=16)
+    return prob, run_oracle(prob)
+
+
+@pytest.mark.parametrize("solve", [B.KF_SOLVE_FP32, B.KF_SOLVE_FP64_TC])
+def test_mixed_long_epoch_T300(long_epoch, solve):
+    """Mixed path over a 300-step epoch (Joseph form every 16 steps, float32 store), the
+    configuration of the N = 8196 benchmark at N = 1024: rounding errors must not build up
+    through the filter's random walk or the smoother's recursions beyond the mixed tolerances."""
+    prob, ref = long_epoch
+    out = solver.run(prob, prec=B.KF_PREC_MIXED_BF16X3, solve_prec=solve, joseph_every=16)
     errs = dict(x_filt=rel_err_per_step(out["x_filt"], ref["x_filt"]),
                 x_smooth=rel_err_per_step(out["x_smooth"], ref["x_smooth"]),
                 diagP_filt=rel_err_elementwise(out["diagP_filt"], diag_of(ref["P_filt"])),
                 diagP_smooth=rel_err_elementwise(out["diagP_smooth"], diag_of(ref["P_smooth"])))
-    print("mixed N=1024 m=306 T=300 errors vs oracle:", errs)
+    print(f"mixed (solve {solve}) N=1024 m=306 T=300 errors vs oracle:", errs)
     check(out, ref, TOL_MEAN32, TOL_DIAG32)
 
 
