@@ -286,7 +286,6 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
   const bool skip = *skip_flag != 0 || nk <= 0;
-  const int nchunks = (nk + C::CK - 1) / C::CK;
   bool mma_issued = false;
 
   if (skip) {
@@ -329,12 +328,18 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t st = base + s * C::STAGE_BYTES;
-      const int c = it / C::CK;
-      const bool first = (it % C::CK) == 0;
-      const bool last = (it % C::CK) == C::CK - 1 || it == nk - 1;
+      const uint64_t adesc0 = smem_desc_sw(st, C::SBO, C::LAYOUT);
+      const uint64_t bdesc0 = smem_desc_sw(st + LV * C::A_BYTES, C::SBO, C::LAYOUT);
 #pragma unroll
       for (int l = 0; l < LV; ++l) {
-        if (first && c > 0 && !mbar_wait(drained_bar(l), (uint32_t)(c - 1) & 1u, abort_flag, a.wait_ns)) {
+        // level l's exact chunks are staggered by l stages, so at most one level changes chunk at
+        // a stage and its drain overlaps the other levels' MMAs
+        const int pos = (it + l) % C::CK;
+        const bool first = pos == 0 || it == 0;
+        const bool last = pos == C::CK - 1 || it == nk - 1;
+        // chunk k of level l covers stages [k CK - l, (k + 1) CK - l): the drain of chunk k - 1 ended
+        if (first && it > 0 &&
+            !mbar_wait(drained_bar(l), (uint32_t)((it + l) / C::CK - 1) & 1u, abort_flag, a.wait_ns)) {
           *abort_flag = 1;
           status_set(a.e.status, KF_ERR_TIMEOUT, a.e.step, 13);
           ok = false;
@@ -348,9 +353,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
 #pragma unroll
           for (int kk = 0; kk < BK / 16; ++kk) {
             const uint32_t acc = (first && pa == 0 && kk == 0) ? 0u : 1u;
-            mma_bf16(dacc, smem_desc_sw(st + pa * C::A_BYTES + kk * 32, C::SBO, C::LAYOUT),
-                     smem_desc_sw(st + LV * C::A_BYTES + pb * C::B_BYTES + kk * 32, C::SBO, C::LAYOUT), C::IDESC,
-                     acc);
+            // the start-address field (bits 0-13, 16-byte units) absorbs the in-stage offsets
+            mma_bf16(dacc, adesc0 + (uint64_t)((pa * C::A_BYTES + kk * 32) >> 4),
+                     bdesc0 + (uint64_t)((pb * C::B_BYTES + kk * 32) >> 4), C::IDESC, acc);
           }
         }
         mma_issued = true;
@@ -366,10 +371,13 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
 #pragma unroll
     for (int j = 0; j < 16; ++j) hi[j] = lo[j] = 0;
     bool ok = true;
-    for (int c = 0; c < nchunks && ok; ++c) {
-#pragma unroll
-      for (int l = 0; l < LV; ++l) {
-        if (!mbar_wait(ready_bar(l), (uint32_t)c & 1u, abort_flag, a.wait_ns)) {
+    // drain events in the MMA issuer's order: at stage it, the level whose staggered chunk ends
+    // there; at the last stage, every level
+    for (int it = 0; it < nk && ok; ++it) {
+      const bool final_stage = it == nk - 1;
+      const int lone = (C::CK - 1 - it % C::CK);  // the level whose chunk ends at stage it
+      for (int l = final_stage ? 0 : lone; l < (final_stage ? LV : min(lone + 1, LV)); ++l) {
+        if (!mbar_wait(ready_bar(l), (uint32_t)((it + l) / C::CK) & 1u, abort_flag, a.wait_ns)) {
           if (!*abort_flag) {
             *abort_flag = 1;
             status_set(a.e.status, KF_ERR_TIMEOUT, a.e.step, 14);
@@ -383,32 +391,86 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncwarp();
         if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(drained_bar(l)) : "memory");
+        const int sh = l < 3 ? 8 * (2 - l) : 8 * (LV - 1 - l);
+        if (l < 3) {
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const long long v = (long long)__float2int_rn(__uint_as_float(r[j]));
-          if (l < 3)
-            hi[j] += v << (8 * (2 - l));
-          else
-            lo[j] += v << (8 * (LV - 1 - l));
+          for (int j = 0; j < 16; ++j) hi[j] += __float2ll_rn(__uint_as_float(r[j])) << sh;
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) lo[j] += __float2ll_rn(__uint_as_float(r[j])) << sh;
         }
       }
     }
-    if (ok && !*abort_flag && gi < a.M) {
-      const int ei = a.ea[gi];
-      double* part = a.partials ? a.partials + (int64_t)blockIdx.y * a.M * a.N : nullptr;
+    // Stage the tile's product values in shared memory (the operand stages are idle once the last
+    // chunk has been drained), then sweep it by rows for the direct outputs (lane -> column, so every
+    // warp access is contiguous) and by columns for the mirrored and transposed outputs.
+    constexpr int PITCH = OZ_BN + 1;  // odd pitch: row and column sweeps are both conflict-free
+    static_assert((size_t)OZ_BM * PITCH * sizeof(double) <= (size_t)C::STAGES * C::STAGE_BYTES, "tile fits");
+    double* tile = reinterpret_cast<double*>(gbase);
+    if (ok) {
+      const int ei = gi < a.M ? a.ea[gi] : 0;
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
         const int gj = n0 + h * 16 + j;
-        if (gj < a.N && !(a.e.sym && gj > gi)) {
-          const int ej = a.eb[gj];
-          const int sc = ei + ej - 14;
-          const double cval = (ei == kOzBadRow || ej == kOzBadRow)
-                                  ? __longlong_as_double(0x7ff8000000000000ll)  // a non-finite operand row
-                                  : scalbn((double)hi[j], sc - 16) + scalbn((double)lo[j], sc - 8 * (LV - 1));
-          if (part)
-            part[(int64_t)gi * a.N + gj] = cval;
-          else
-            oz_apply(a.e, gi, gj, cval);
+        const int ej = gj < a.N ? a.eb[gj] : 0;
+        const int sc = ei + ej - 14;
+        tile[(32 * q + lane) * PITCH + h * 16 + j] =
+            (ei == kOzBadRow || ej == kOzBadRow)
+                ? __longlong_as_double(0x7ff8000000000000ll)  // a non-finite operand row
+                : scalbn((double)hi[j], sc - 16) + scalbn((double)lo[j], sc - 8 * (LV - 1));
+      }
+    }
+    asm volatile("bar.sync 1, %0;" ::"n"(32 * OZ_EPI_WARPS) : "memory");
+    const bool go = !*abort_flag;
+    const int ew = warp - 2;  // epilogue warp 0..15
+    const OzEpilogue& e = a.e;
+    double* part = a.partials ? a.partials + (int64_t)blockIdx.y * a.M * a.N : nullptr;
+    if (go) {
+      for (int r = ew; r < OZ_BM; r += OZ_EPI_WARPS) {
+        const int gi2 = m0 + r;
+        if (gi2 >= a.M) break;
+#pragma unroll
+        for (int cc = 0; cc < OZ_BN; cc += 32) {
+          const int c = cc + lane, gj = n0 + c;
+          if (gj >= a.N || (e.sym && gj > gi2)) continue;
+          const double cval = tile[r * PITCH + c];
+          if (part) {
+            part[(int64_t)gi2 * a.N + gj] = cval;
+            continue;
+          }
+          double v = e.alpha * cval;
+          if (e.cin) v += e.beta * e.cin[(int64_t)gi2 * e.ldcin + gj];
+          if (gi2 == gj) v += e.delta;
+          if (e.radd_kind >= 0) v += oz_qv(e.radd_kind, e.radd, e.ldradd, gi2, gj);
+          if (e.out) e.out[(int64_t)gi2 * e.ldo + gj] = v;
+          if (e.outf) e.outf[(int64_t)gi2 * e.ldof + gj] = (float)v;
+          if (e.out2) e.out2[(int64_t)gi2 * e.ldo2 + gj] = v + oz_qv(e.q_kind, e.q, e.ldq, gi2, gj);
+          if (gi2 == gj) {
+            if (e.diag_out) e.diag_out[gi2] = v;
+            if (e.check_diag && !(v > 0.0 && isfinite(v))) status_set(e.status, KF_ERR_NUMERIC, e.step, gi2);
+          }
+          tile[r * PITCH + c] = v;  // for the column sweep
+        }
+      }
+    }
+    if (!part && (e.sym || e.outT)) {
+      asm volatile("bar.sync 1, %0;" ::"n"(32 * OZ_EPI_WARPS) : "memory");
+      if (go) {
+        for (int c = ew; c < OZ_BN; c += OZ_EPI_WARPS) {
+          const int gj = n0 + c;
+          if (gj >= a.N) break;
+#pragma unroll
+          for (int rr = 0; rr < OZ_BM; rr += 32) {
+            const int r = rr + lane, gi2 = m0 + r;
+            if (gi2 >= a.M || (e.sym && gj > gi2)) continue;
+            const double v = tile[r * PITCH + c];
+            if (e.outT) e.outT[(int64_t)gj * e.ldoT + gi2] = v;
+            if (e.sym && gi2 != gj) {  // mirror (gj, gi2): consecutive lanes write consecutive columns
+              if (e.out) e.out[(int64_t)gj * e.ldo + gi2] = v;
+              if (e.outf) e.outf[(int64_t)gj * e.ldof + gi2] = (float)v;
+              if (e.out2) e.out2[(int64_t)gj * e.ldo2 + gi2] = v + oz_qv(e.q_kind, e.q, e.ldq, gj, gi2);
+            }
+          }
         }
       }
     }
