@@ -140,7 +140,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp32", "fp64"])
-    ap.add_argument("--solve", default="fp32", choices=["fp32", "fp64", "fp64tc"],
+    ap.add_argument("--solve", default="fp32", choices=["fp32", "fp64", "fp64tc", "fp64mean"],
                     help="smoother-gain solve: float32 class, float64 on the CUDA cores, or float64-accurate on "
                          "the tensor cores (float32-class factor + Newton steps with exact-slice residuals)")
     ap.add_argument("--T", type=int, default=T_STEPS, help="time steps per epoch (the workload uses 300)")
@@ -282,7 +282,8 @@ def main():
     build.build()
     B.lib()
     prec = {"mixed": B.KF_PREC_MIXED_BF16X3, "fp32": B.KF_PREC_FP32, "fp64": B.KF_PREC_FP64}[args.prec]
-    solve = {"fp32": B.KF_SOLVE_FP32, "fp64": B.KF_SOLVE_FP64, "fp64tc": B.KF_SOLVE_FP64_TC}[args.solve]
+    solve = {"fp32": B.KF_SOLVE_FP32, "fp64": B.KF_SOLVE_FP64, "fp64tc": B.KF_SOLVE_FP64_TC,
+             "fp64mean": B.KF_SOLVE_FP64_MEAN}[args.solve]
     T = args.T
     prob = synth.config2(T=T)
     d = solver.upload(prob)
@@ -515,7 +516,8 @@ def config2_mesh_sample(args, B, solver, synth, torch):
     budget = 160 * 10 ** 9
     rule = 2 * prob.N * prob.N * prob.T * 4
     ck = int(round(np.sqrt(prob.T))) if rule > budget else 0
-    solve = {"fp32": B.KF_SOLVE_FP32, "fp64": B.KF_SOLVE_FP64, "fp64tc": B.KF_SOLVE_FP64_TC}[args.solve]
+    solve = {"fp32": B.KF_SOLVE_FP32, "fp64": B.KF_SOLVE_FP64, "fp64tc": B.KF_SOLVE_FP64_TC,
+             "fp64mean": B.KF_SOLVE_FP32}[args.solve]  # the mean-only refinement needs F = I or dense F
     r, dt, ck_used = _epoch_rate(prob, B, solver, torch, prec=B.KF_PREC_MIXED_BF16X3, solve_prec=solve,
                                  joseph_every=16, mem_budget_bytes=budget, checkpoint_every=ck)
     return {"workload": prob.name, "value": r, "unit": "timesteps/s", "s": dt, "checkpoint_every": ck_used,

@@ -69,11 +69,18 @@ typedef enum {
                              /* cores                                                */
   KF_SOLVE_FP32 = 1,         /* float32 class: float32 factor (split-bf16 tensor-core */
                              /* products in KF_PREC_MIXED_BF16X3)                    */
-  KF_SOLVE_FP64_TC = 2       /* float64 accuracy on the tensor cores (needs          */
+  KF_SOLVE_FP64_TC = 2,      /* float64 accuracy on the tensor cores (needs          */
                              /* KF_PREC_MIXED_BF16X3): the float32-class inverse of  */
                              /* P_{t+1|t} refined by two Newton steps whose residuals */
                              /* I - P X are exact-slice products (kfx_spd_inverse    */
                              /* mode 2); J_t in float64 for the smoothed mean        */
+  KF_SOLVE_FP64_MEAN = 3     /* needs KF_PREC_MIXED_BF16X3 and F = I or dense: the   */
+                             /* smoothed mean's solve y = P_{t+1|t}^{-1} d (eqn 12)  */
+                             /* refined to float64 accuracy (float64 residuals       */
+                             /* d - P y, the float32-class inverse as preconditioner, */
+                             /* three steps), x_{t|T} = x_{t|t} + P_{t|t} F^T y;     */
+                             /* J_t inside the split-bf16 covariance product of      */
+                             /* eqn 13 from the float32-class inverse                */
 } kf_solve_precision;
 
 typedef enum { KF_COV_SCALAR = 0, KF_COV_DIAG = 1, KF_COV_DENSE = 2 } kf_cov_kind;

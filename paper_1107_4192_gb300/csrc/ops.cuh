@@ -113,6 +113,23 @@ template <typename T>
 kf_status gemv(cudaStream_t s, int64_t rows, int64_t cols, const T* A, int64_t lda,
                const double* x, const double* ybase, double sign, double* y);
 
+// As gemv for a float32 matrix with float64 products and sums (a float64-accurate product of
+// the float32 values, e.g. a residual d - P y).
+kf_status gemv_f64acc(cudaStream_t s, int64_t rows, int64_t cols, const float* A, int64_t lda, const double* x,
+                      const double* ybase, double sign, double* y);
+
+// y[j] = sum_i A[i, j] x[i] (float64), y = ybase + sign A^T x when ybase.
+kf_status gemv_t(cudaStream_t s, int64_t rows, int64_t cols, const double* A, int64_t lda, const double* x,
+                 const double* ybase, double sign, double* y);
+
+// J = I - Q X (n x n float32) for Q = q I (q_kind 0) or diagonal (q_kind 1).
+kf_status identity_minus_q(cudaStream_t s, int64_t n, const float* X, int64_t ldx, int q_kind, const double* q,
+                           float* J, int64_t ldj);
+
+// out = a + d - Q y for Q = q I (q_kind 0) or diagonal (q_kind 1), float64 vectors.
+kf_status mean_update_q(cudaStream_t s, int64_t n, const double* a, const double* d, int q_kind, const double* q,
+                        const double* yv, double* out);
+
 // status[ST_CUR] = step (read by graph-replayed kernels that report failures)
 kf_status set_status_step(cudaStream_t s, int* status, int step);
 

@@ -231,6 +231,29 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const T* X, int64_t ld, i
   }
 }
 
+// One level's drain by an epilogue warp: read its 16 accumulator columns (exact integers below
+// 2^24), hand the accumulator back to the MMA issuer, and add the values into the 64-bit fixed-point
+// sums (levels 0-2 in units of level 2, levels 3.. in units of level LV-1).
+template <int L, int LV>
+__device__ __forceinline__ void oz_drain(uint32_t taddr, uint32_t dbar, int lane, long long (&hi)[16],
+                                         long long (&lo)[16]) {
+  if constexpr (L < LV) {
+    uint32_t r[16];
+    tmem_ld16(taddr, r);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncwarp();
+    if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(dbar) : "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const long long v = (long long)__float2int_rn(__uint_as_float(r[j]));
+      if constexpr (L < 3)
+        hi[j] += v << (8 * (2 - L));
+      else
+        lo[j] += v << (8 * (LV - 1 - L));
+    }
+  }
+}
+
 template <int LV, int BK>
 __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_constant__ OzMaps maps, const OzArgs a) {
   using C = OzCfg<LV, BK>;
@@ -386,18 +409,18 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        uint32_t r[16];
-        tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(l * OZ_BN + h * 16), r);
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncwarp();
-        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(drained_bar(l)) : "memory");
-        const int sh = l < 3 ? 8 * (2 - l) : 8 * (LV - 1 - l);
-        if (l < 3) {
-#pragma unroll
-          for (int j = 0; j < 16; ++j) hi[j] += __float2ll_rn(__uint_as_float(r[j])) << sh;
-        } else {
-#pragma unroll
-          for (int j = 0; j < 16; ++j) lo[j] += __float2ll_rn(__uint_as_float(r[j])) << sh;
+        const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(l * OZ_BN + h * 16);
+        const uint32_t dbar = drained_bar(l);
+        // compile-time level, so the shifts are constants and the conversions 32-bit
+        switch (l) {
+          case 0: oz_drain<0, LV>(taddr, dbar, lane, hi, lo); break;
+          case 1: oz_drain<1, LV>(taddr, dbar, lane, hi, lo); break;
+          case 2: oz_drain<2, LV>(taddr, dbar, lane, hi, lo); break;
+          case 3: oz_drain<3, LV>(taddr, dbar, lane, hi, lo); break;
+          case 4: oz_drain<4, LV>(taddr, dbar, lane, hi, lo); break;
+          case 5: oz_drain<5, LV>(taddr, dbar, lane, hi, lo); break;
+          case 6: oz_drain<6, LV>(taddr, dbar, lane, hi, lo); break;
+          default: break;
         }
       }
     }

@@ -45,6 +45,9 @@ struct kf_plan_s {
   int64_t N = 0, m = 0, T = 0, ldN = 0, ldm = 0;
   int bulk = 0, solve = 0;
   bool refine = false;    // KF_SOLVE_FP64_TC: float64-accurate inverse of P_{t+1|t}
+  bool mean_refine = false;  // KF_SOLVE_FP64_MEAN: float64-accurate solve of the smoothed mean
+  float* X0f = nullptr;      // W^T W (KF_SOLVE_FP64_MEAN)
+  double *ysol = nullptr, *rsol = nullptr, *wsol = nullptr;  // its vectors
   int smooth_slices = 2;  // bf16 planes per operand in the smoother products (mixed mode)
   size_t b = 8, sb = 8;   // bytes per bulk / solve element
   int64_t ckpt = 1;       // 1 = every P_{t|t} stored
@@ -134,6 +137,7 @@ Sizes sizes_for(const kf_desc* d) {
   w += (z.sb != z.b ? z.slot : 0) + 3 * z.slot;                            // Jm, Wb, Db, Pn
   if (d->prec == KF_PREC_MIXED_BF16X3 && z.sb == 4) w += z.slot;         // Wi
   if (d->solve_prec == KF_SOLVE_FP64_TC) w += refine_bytes(N, ldN) + N * ldN * 8;  // refinement, J in float64
+  if (d->solve_prec == KF_SOLVE_FP64_MEAN) w += z.slot + 3 * N * 8;                 // W^T W, vectors
   if (d->prec == KF_PREC_MIXED_BF16X3) {
     // exact-slice filter: U, L^{-1}, L^{-T}, [K V], [V K], S partials, slices
     w += m * ldN * 8 + 2 * m * m * 8 + (d->joseph_every > 0 ? 4 * N * ldm * 8 : 0) + kOzSplitsS * m * m * 8 + 8;
@@ -160,8 +164,10 @@ kf_status validate(const kf_desc* d) {
   if (d->f_kind < 0 || d->f_kind > 2) return KF_ERR_ARG;
   if (d->f_kind == KF_F_CSR && d->f_nnz < 1) return KF_ERR_ARG;
   if (d->prec < 0 || d->prec > 2) return KF_ERR_ARG;
-  if (d->solve_prec < 0 || d->solve_prec > 2) return KF_ERR_ARG;
-  if (d->solve_prec == KF_SOLVE_FP64_TC && d->prec != KF_PREC_MIXED_BF16X3) return KF_ERR_ARG;
+  if (d->solve_prec < 0 || d->solve_prec > 3) return KF_ERR_ARG;
+  if ((d->solve_prec == KF_SOLVE_FP64_TC || d->solve_prec == KF_SOLVE_FP64_MEAN) && d->prec != KF_PREC_MIXED_BF16X3)
+    return KF_ERR_ARG;
+  if (d->solve_prec == KF_SOLVE_FP64_MEAN && d->f_kind == KF_F_CSR) return KF_ERR_UNSUPPORTED;
   if (d->q_kind < 0 || d->q_kind > 2 || d->r_kind < 0 || d->r_kind > 2) return KF_ERR_ARG;
   if (d->joseph_every < 0 || d->checkpoint_every < 0) return KF_ERR_ARG;
   if (d->split_terms != 0 && d->split_terms != 3 && d->split_terms != 6) return KF_ERR_ARG;
@@ -840,6 +846,27 @@ kf_status run_smoother(kf_plan_s* p, double* x_smooth, double* diagP_smooth, dou
           g.status = p->status;
           KF_TRY(tc_gemm_ops(s, p->tc, TcOperand{Bm, ldN, 0, 0}, TcOperand{p->rb.X0, ldN, 1, 0}, g, 3));
         }
+      } else if (tc_solve && p->mean_refine) {
+        // the float32-class inverse X0 = W^T W: preconditioner of the mean's solve below and, for
+        // F = I with a scalar or diagonal Q, the gain J = I - Q X0 of the covariance products
+        GemmParams<float> g;
+        g.M = (int)N; g.N = (int)N; g.K = (int)N;
+        g.out = p->X0f; g.ldo = ldN;
+        g.sym = 1;
+        g.tri_a = -1;
+        g.tri_b = -1;
+        g.status = p->status;
+        KF_TRY(tc_gemm_ops(s, p->tc, TcOperand{p->Wi, ldN, 0, 1}, TcOperand{p->Wi, ldN, 0, 1}, g, 3));
+        if (p->d.f_kind == KF_F_IDENTITY && p->d.q_kind != KF_COV_DENSE) {
+          KF_TRY(identity_minus_q(s, N, p->X0f, ldN, p->d.q_kind, p->Q, (float*)Jb, ldN));
+        } else {
+          if (Bm != Pt) {  // Bm lives in tmpN, which the products below use as scratch
+            KF_TRY((copy2d<B, B>(s, (B*)Jb, ldN, Bm, ldN, N, N)));
+            Bm = (const B*)Jb;
+          }
+          KF_TRY(gain_from_inverse_tc(s, p->tc, (int)N, (const float*)Bm, ldN, p->Wi, ldN, (float*)p->tmpN, ldN,
+                                      (float*)Jb, ldN, p->status));
+        }
       } else if (tc_solve && p->d.f_kind == KF_F_IDENTITY && p->d.q_kind != KF_COV_DENSE) {
         KF_TRY(gain_identity_tc(s, p->tc, (int)N, p->Wi, ldN, p->d.q_kind, p->Q, (float*)Jb, ldN, p->status));
       } else if (tc_solve) {
@@ -857,9 +884,25 @@ kf_status run_smoother(kf_plan_s* p, double* x_smooth, double* diagP_smooth, dou
     }
     // x_{t|T} = x_{t|t} + J_t (x_{t+1|T} - x_{t+1|t})
     KF_TRY(vsub(s, N, p->xs + (t + 1) * N, p->xpred + (t + 1) * N, p->dx));
-    if (p->refine)
+    if (p->refine) {
       KF_TRY(gemv<double>(s, N, N, p->J64, ldN, p->dx, p->xfilt + t * N, 1.0, p->xs + t * N));
-    else
+    } else if (p->mean_refine) {
+      // y = P_{t+1|t}^{-1} dx by iterative refinement: float64 residuals r = dx - P y against the
+      // float32 P_{t+1|t}, corrections y += X0 r with the float32-class inverse (each step shrinks
+      // the error by |I - X0 P| ~ 1e-5); then x_{t|T} = x_{t|t} + P_{t|t} F^T y
+      const float* Pp = (const float*)Pn;
+      KF_TRY(gemv<float>(s, N, N, p->X0f, ldN, p->dx, nullptr, 1.0, p->ysol));
+      for (int k = 0; k < 3; ++k) {
+        KF_TRY(gemv_f64acc(s, N, N, Pp, ldN, p->ysol, p->dx, -1.0, p->rsol));
+        KF_TRY(gemv<float>(s, N, N, p->X0f, ldN, p->rsol, p->ysol, 1.0, p->ysol));
+      }
+      const double* w = p->ysol;
+      if (p->d.f_kind == KF_F_DENSE) {  // w = F^T y
+        KF_TRY(gemv_t(s, N, N, p->F, N, p->ysol, nullptr, 1.0, p->wsol));
+        w = p->wsol;
+      }
+      KF_TRY(gemv_f64acc(s, N, N, (const float*)Pt, ldN, w, p->xfilt + t * N, 1.0, p->xs + t * N));
+    } else
       KF_TRY(gemv<V>(s, N, N, Jb, ldN, p->dx, p->xfilt + t * N, 1.0, p->xs + t * N));
     if ((void*)Jm != (void*)Jb) KF_TRY((copy2d<B, V>(s, Jm, ldN, Jb, ldN, N, N)));
     {
@@ -964,6 +1007,7 @@ kf_status kf_plan(kf_plan_t* out, const kf_desc* d) {
   p->bulk = d->prec == KF_PREC_FP64 ? BULK_F64 : d->prec == KF_PREC_FP32 ? BULK_F32 : BULK_BF16X3;
   p->solve = z.sb == 8 ? 0 : 1;
   p->refine = d->solve_prec == KF_SOLVE_FP64_TC;
+  p->mean_refine = d->solve_prec == KF_SOLVE_FP64_MEAN;
   p->smooth_slices = d->split_terms == 6 ? 3 : 2;
   p->slot = z.slot;
   p->ckpt = c;
@@ -1001,6 +1045,12 @@ kf_status kf_plan(kf_plan_t* out, const kf_desc* d) {
   A(&p->Ldinv, round_up(N, nbs) * nbs * sb);
   if (sb != b) A(&p->Jm, p->slot);
   if (p->bulk == BULK_BF16X3 && sb == 4) A(&p->Wi, p->slot);
+  if (p->mean_refine) {
+    A(&p->X0f, p->slot);
+    A(&p->ysol, N * 8);
+    A(&p->rsol, N * 8);
+    A(&p->wsol, N * 8);
+  }
   if (p->refine) {
     char* rm = nullptr;
     A(&rm, refine_bytes(N, ldN));

@@ -165,14 +165,14 @@ kf_status add_cov(cudaStream_t s, Tdst* dst, int64_t ldd, const Tsrc* src, int64
 // 32 lane sums are combined in float64.
 constexpr int kGemvSmemX = 12288;
 
-template <typename T>
+template <typename T, bool F64ACC>
 __global__ void __launch_bounds__(256) gemv_kernel(int64_t rows, int64_t cols, const T* A, int64_t lda,
                                                    const double* x, const double* ybase, double sign, double* y) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const bool vec = aligned_rows(A, lda);
-  if constexpr (sizeof(T) == 4) {
+  if constexpr (sizeof(T) == 4 && !F64ACC) {
     __shared__ float xs[kGemvSmemX];
     if (cols <= kGemvSmemX) {
       for (int64_t j = threadIdx.x; j < cols; j += blockDim.x) xs[j] = (float)x[j];
@@ -219,9 +219,72 @@ kf_status gemv(cudaStream_t s, int64_t rows, int64_t cols, const T* A, int64_t l
   // float32 rows: 16 rows per block (x is converted once per block)
   const int64_t per_block_rows = sizeof(T) == 4 ? 16 : 8;
   unsigned blocks = (unsigned)std::min<int64_t>(ceil_div(rows, per_block_rows), 4096);
-  gemv_kernel<T><<<blocks, 256, 0, s>>>(rows, cols, A, lda, x, ybase, sign, y);
+  gemv_kernel<T, false><<<blocks, 256, 0, s>>>(rows, cols, A, lda, x, ybase, sign, y);
   note_launch();
   return launch_check("gemv");
+}
+
+kf_status gemv_f64acc(cudaStream_t s, int64_t rows, int64_t cols, const float* A, int64_t lda, const double* x,
+                      const double* ybase, double sign, double* y) {
+  if (rows <= 0) return KF_OK;
+  unsigned blocks = (unsigned)std::min<int64_t>(ceil_div(rows, 8), 4096);
+  gemv_kernel<float, true><<<blocks, 256, 0, s>>>(rows, cols, A, lda, x, ybase, sign, y);
+  note_launch();
+  return launch_check("gemv_f64acc");
+}
+
+// y = ybase + sign A^T x: one thread per column, consecutive threads read consecutive columns.
+__global__ void gemv_t_kernel(int64_t rows, int64_t cols, const double* A, int64_t lda, const double* x,
+                              const double* ybase, double sign, double* y) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < cols; j += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int64_t i = 0; i < rows; ++i) acc = fma(A[i * lda + j], x[i], acc);
+    y[j] = ybase ? ybase[j] + sign * acc : acc;
+  }
+}
+
+kf_status gemv_t(cudaStream_t s, int64_t rows, int64_t cols, const double* A, int64_t lda, const double* x,
+                 const double* ybase, double sign, double* y) {
+  if (cols <= 0) return KF_OK;
+  gemv_t_kernel<<<(unsigned)std::min<int64_t>(ceil_div(cols, 128), 1024), 128, 0, s>>>(rows, cols, A, lda, x, ybase,
+                                                                                   sign, y);
+  note_launch();
+  return launch_check("gemv_t");
+}
+
+// J = I - Q X for Q = q I (q_kind 0) or diagonal (1): row i scaled by q_i.
+__global__ void identity_minus_q_kernel(int64_t n, const float* X, int64_t ldx, int q_kind, const double* q, float* J,
+                                        int64_t ldj) {
+  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n * n; u += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = u / n, j = u % n;
+    const float qi = (float)(q_kind == 0 ? q[0] : q[i]);
+    J[i * ldj + j] = (i == j ? 1.0f : 0.0f) - qi * X[i * ldx + j];
+  }
+}
+
+kf_status identity_minus_q(cudaStream_t s, int64_t n, const float* X, int64_t ldx, int q_kind, const double* q,
+                           float* J, int64_t ldj) {
+  if (q_kind != 0 && q_kind != 1) return KF_ERR_ARG;
+  identity_minus_q_kernel<<<(unsigned)std::min<int64_t>(ceil_div(n * n, 256), 152 * 16), 256, 0, s>>>(n, X, ldx,
+                                                                                                  q_kind, q, J, ldj);
+  note_launch();
+  return launch_check("identity_minus_q");
+}
+
+// out = a + d - Q y (Q per q_kind: scalar or diagonal).
+__global__ void mean_update_q_kernel(int64_t n, const double* a, const double* d, int q_kind, const double* q,
+                                     const double* yv, double* out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = a[i] + (d[i] - (q_kind == 0 ? q[0] : q[i]) * yv[i]);
+}
+
+kf_status mean_update_q(cudaStream_t s, int64_t n, const double* a, const double* d, int q_kind, const double* q,
+                        const double* yv, double* out) {
+  if (q_kind != 0 && q_kind != 1) return KF_ERR_ARG;
+  mean_update_q_kernel<<<(unsigned)std::min<int64_t>(ceil_div(n, 256), 1024), 256, 0, s>>>(n, a, d, q_kind, q, yv,
+                                                                                          out);
+  note_launch();
+  return launch_check("mean_update_q");
 }
 
 __global__ void set_step_kernel(int* status, int step) { status[ST_CUR] = step; }

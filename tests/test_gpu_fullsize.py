@@ -37,10 +37,11 @@ def oracle_T2():
     return run_oracle(synth.config2(T=2))
 
 
-@pytest.mark.parametrize("mode", ["mixed", "mixed_fp64tc", "fp64"])
+@pytest.mark.parametrize("mode", ["mixed", "mixed_fp64tc", "mixed_fp64mean", "fp64"])
 def test_fullsize_vs_oracle_prefix(oracle_T2, mode):
     prob = synth.config2(T=2)
-    kw = {"mixed": MIXED, "mixed_fp64tc": MIXED64, "fp64": dict(prec=B.KF_PREC_FP64)}[mode]
+    kw = {"mixed": MIXED, "mixed_fp64tc": MIXED64, "fp64": dict(prec=B.KF_PREC_FP64),
+          "mixed_fp64mean": dict(prec=B.KF_PREC_MIXED_BF16X3, solve_prec=B.KF_SOLVE_FP64_MEAN)}[mode]
     out = solver.run(prob, **kw)
     ref = oracle_T2
     tm, td = (1e-4, 1e-3) if mode.startswith("mixed") else (1e-10, 1e-10)

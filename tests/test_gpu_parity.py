@@ -75,7 +75,7 @@ def test_mixed_bf16x3_paths(solve, mesh):
     check(out, run_oracle(prob), TOL_MEAN32, TOL_DIAG32)
 
 
-@pytest.mark.parametrize("solve", [B.KF_SOLVE_FP32, B.KF_SOLVE_FP64_TC])
+@pytest.mark.parametrize("solve", [B.KF_SOLVE_FP32, B.KF_SOLVE_FP64_TC, B.KF_SOLVE_FP64_MEAN])
 @pytest.mark.parametrize("N,m,T", [(129, 20, 4), (257, 70, 5), (600, 64, 4), (200, 306, 5), (512, 306, 6)])
 def test_mixed_ragged_sizes(N, m, T, solve):
     prob = synth.random_walk_problem(N, m, T, seed=N + m)
@@ -128,7 +128,8 @@ def test_mixed_checkpoint_recompute(mesh, c, solve):
     (B.KF_PREC_FP32, B.KF_SOLVE_FP64, TOL_MEAN32, TOL_DIAG32),
     (B.KF_PREC_MIXED_BF16X3, B.KF_SOLVE_FP32, TOL_MEAN32, TOL_DIAG32),
     (B.KF_PREC_MIXED_BF16X3, B.KF_SOLVE_FP64, TOL_MEAN32, TOL_DIAG32),
-    (B.KF_PREC_MIXED_BF16X3, B.KF_SOLVE_FP64_TC, TOL_MEAN32, TOL_DIAG32)])
+    (B.KF_PREC_MIXED_BF16X3, B.KF_SOLVE_FP64_TC, TOL_MEAN32, TOL_DIAG32),
+    (B.KF_PREC_MIXED_BF16X3, B.KF_SOLVE_FP64_MEAN, TOL_MEAN32, TOL_DIAG32)])
 @pytest.mark.parametrize("N,m,T", [(200, 20, 8), (257, 70, 5)])
 def test_dense_F(prec, solve, tm, td, N, m, T):
     """General dense, non-symmetric F passed as a dense N x N matrix (KF_F_DENSE), dense Q, R, P0."""
@@ -153,7 +154,7 @@ def long_epoch():
     return prob, run_oracle(prob)
 
 
-@pytest.mark.parametrize("solve", [B.KF_SOLVE_FP32, B.KF_SOLVE_FP64_TC])
+@pytest.mark.parametrize("solve", [B.KF_SOLVE_FP32, B.KF_SOLVE_FP64_TC, B.KF_SOLVE_FP64_MEAN])
 def test_mixed_long_epoch_T300(long_epoch, solve):
     """Mixed path over a 300-step epoch (Joseph form every 16 steps, float32 store), the
     configuration of the N = 8196 benchmark at N = 1024: rounding errors must not build up
@@ -166,6 +167,36 @@ def test_mixed_long_epoch_T300(long_epoch, solve):
                 diagP_smooth=rel_err_elementwise(out["diagP_smooth"], diag_of(ref["P_smooth"])))
     print(f"mixed (solve {solve}) N=1024 m=306 T=300 errors vs oracle:", errs)
     check(out, ref, TOL_MEAN32, TOL_DIAG32)
+
+
+@pytest.mark.parametrize("solve", [B.KF_SOLVE_FP64_TC, B.KF_SOLVE_FP64_MEAN])
+@pytest.mark.parametrize("dense", [False, True])
+def test_fp64_accurate_solves_match_the_cuda_core_solve(solve, dense):
+    """With the same mixed filter (float64-class, so filtered means and stored P_{t|t} are the
+    same launch sequence), the smoothed means of the float64-accurate tensor-core solves equal
+    those of the float64 CUDA-core solve (Cholesky + two triangular solves) to float64 rounding
+    times the conditioning, far below the float32-class solve's difference."""
+    prob = synth.dense_dynamics_problem(384, 40, 12, seed=5) if dense else synth.mesh_problem(
+        600, 64, 12, seed=7, identity_F=True)
+    kw = dict(prec=B.KF_PREC_MIXED_BF16X3, joseph_every=4, dense_F=dense)
+    ref = solver.run(prob, solve_prec=B.KF_SOLVE_FP64, **kw)
+    out = solver.run(prob, solve_prec=solve, **kw)
+    f32 = solver.run(prob, solve_prec=B.KF_SOLVE_FP32, **kw)
+    assert np.array_equal(out["x_filt"], ref["x_filt"])
+    e = rel_err_per_step(out["x_smooth"], ref["x_smooth"])
+    e32 = rel_err_per_step(f32["x_smooth"], ref["x_smooth"])
+    print(f"solve {solve} dense {dense}: smoothed means vs float64 solve {e:.2e} (float32-class solve {e32:.2e})")
+    assert e <= 1e-10
+    assert rel_err_elementwise(out["diagP_smooth"], ref["diagP_smooth"]) <= TOL_DIAG32
+
+
+def test_fp64_mean_solve_rejects_compressed_row_F():
+    prob = synth.mesh_problem(64, 8, 3, seed=1)
+    d = solver.upload(prob)
+    with pytest.raises(B.KfError) as e:
+        solver.Plan.for_inputs(d, prob.N, prob.m, prob.T, prec=B.KF_PREC_MIXED_BF16X3,
+                               solve_prec=B.KF_SOLVE_FP64_MEAN)
+    assert e.value.status == B.KF_ERR_UNSUPPORTED
 
 
 def test_full_smoothed_covariance_output():
