@@ -43,7 +43,7 @@ constexpr int kOzBadRow = 0x7fffffff;  // exponent marking a row that holds an i
 // swizzle, 32: 64-byte swizzle): smaller stages give a deeper pipeline for the same shared memory.
 template <int LV, int BK>
 struct OzCfg {
-  static_assert(BK == 16 || BK == 32, "one 32- or 64-byte swizzle row per stage");
+  static_assert(BK == 16, "one 32-byte swizzle row per stage: one MMA k-step, so A-slice-major MMA order can use the A collector");
   static constexpr int SWZ = BK * 2;                         // swizzle width in bytes
   static constexpr uint32_t LAYOUT = BK == 16 ? kLayoutSw32 : kLayoutSw64;  // descriptor swizzle mode
   static constexpr uint32_t SBO = 8 * SWZ;                   // bytes between 8-row groups
@@ -353,37 +353,45 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
       const uint32_t st = base + s * C::STAGE_BYTES;
       const uint64_t adesc0 = smem_desc_sw(st, C::SBO, C::LAYOUT);
       const uint64_t bdesc0 = smem_desc_sw(st + LV * C::A_BYTES, C::SBO, C::LAYOUT);
+      // level l's exact chunks are staggered by l stages, so at most one level changes chunk at a
+      // stage and its drain overlaps the other levels' MMAs; chunk k of level l covers stages
+      // [k CK - l, (k + 1) CK - l).  The MMAs run A-slice-major (pa outer, pb inner), so the A
+      // collector keeps slice pa for all its partners and A is read from shared memory once.
 #pragma unroll
-      for (int l = 0; l < LV; ++l) {
-        // level l's exact chunks are staggered by l stages, so at most one level changes chunk at
-        // a stage and its drain overlaps the other levels' MMAs
-        const int pos = (it + l) % C::CK;
-        const bool first = pos == 0 || it == 0;
-        const bool last = pos == C::CK - 1 || it == nk - 1;
-        // chunk k of level l covers stages [k CK - l, (k + 1) CK - l): the drain of chunk k - 1 ended
-        if (first && it > 0 &&
-            !mbar_wait(drained_bar(l), (uint32_t)((it + l) / C::CK - 1) & 1u, abort_flag, a.wait_ns)) {
-          *abort_flag = 1;
-          status_set(a.e.status, KF_ERR_TIMEOUT, a.e.step, 13);
-          ok = false;
-          break;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t dacc = tmem + (uint32_t)(l * OZ_BN);
+      for (int pa = 0; pa < LV && ok; ++pa) {
 #pragma unroll
-        for (int pa = 0; pa <= l; ++pa) {
-          const int pb = l - pa;
-#pragma unroll
-          for (int kk = 0; kk < BK / 16; ++kk) {
-            const uint32_t acc = (first && pa == 0 && kk == 0) ? 0u : 1u;
-            // the start-address field (bits 0-13, 16-byte units) absorbs the in-stage offsets
-            mma_bf16(dacc, adesc0 + (uint64_t)((pa * C::A_BYTES + kk * 32) >> 4),
-                     bdesc0 + (uint64_t)((pb * C::B_BYTES + kk * 32) >> 4), C::IDESC, acc);
+        for (int pb = 0; pb < LV - pa; ++pb) {
+          const int l = pa + pb;
+          const int pos = (it + l) % C::CK;
+          const bool first = pos == 0 || it == 0;
+          if (pa == 0 && first && it > 0 &&
+              !mbar_wait(drained_bar(l), (uint32_t)((it + l) / C::CK - 1) & 1u, abort_flag, a.wait_ns)) {
+            *abort_flag = 1;
+            status_set(a.e.status, KF_ERR_TIMEOUT, a.e.step, 13);
+            ok = false;
+            break;
           }
+          if (pa == 0) asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t dacc = tmem + (uint32_t)(l * OZ_BN);
+          const uint32_t acc = (first && pa == 0) ? 0u : 1u;
+          // the start-address field (bits 0-13, 16-byte units) absorbs the in-stage offsets
+          const uint64_t ad = adesc0 + (uint64_t)((pa * C::A_BYTES) >> 4);
+          const uint64_t bd = bdesc0 + (uint64_t)((pb * C::B_BYTES) >> 4);
+          if (LV - pa == 1)
+            mma_bf16_coll<kCollNone>(dacc, ad, bd, C::IDESC, acc);
+          else if (pb == 0)
+            mma_bf16_coll<kCollFill>(dacc, ad, bd, C::IDESC, acc);
+          else if (pb == LV - 1 - pa)
+            mma_bf16_coll<kCollLastUse>(dacc, ad, bd, C::IDESC, acc);
+          else
+            mma_bf16_coll<kCollUse>(dacc, ad, bd, C::IDESC, acc);
         }
         mma_issued = true;
-        if (last) mma_commit(ready_bar(l));
       }
+      if (!ok) break;
+#pragma unroll
+      for (int l = 0; l < LV; ++l)
+        if ((it + l) % C::CK == C::CK - 1 || it == nk - 1) mma_commit(ready_bar(l));
       if (ok) mma_commit(empty_bar(s));
     }
   } else if (warp >= 2) {
