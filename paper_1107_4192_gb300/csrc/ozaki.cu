@@ -54,11 +54,15 @@ struct OzCfg {
   static constexpr int FIT = (210 * 1024) / STAGE_BYTES;
   static constexpr int STAGES = FIT > 8 ? 8 : FIT;
   static_assert(STAGES >= 2, "double-buffered pipeline");
-  static_assert(LV * OZ_BN <= 512, "one TMEM accumulator per level");
+  // NB = LV + 1 accumulators rotate among the levels (chunk k of level l in buffer (l + k) mod NB),
+  // so the buffer a level leaves is drained while the MMAs continue in the spare one
+  static constexpr int NB = LV + 1;
+  static_assert(NB * OZ_BN <= 512, "one TMEM accumulator per level plus a spare");
+  static_assert(LV < CK, "one level changes chunk per stage");
   // a level has at most LV slice pairs whose products are below 2^14 in magnitude, so one
   // chunk of OZ_KC values of k sums to an integer below 2^24: exact in float32
   static_assert(LV * OZ_KC * 16384 <= (1 << 24), "exact chunk");
-  static_assert(2 * STAGES + 2 * LV + 1 <= 28, "barriers fit their 256 bytes");
+  static_assert(2 * STAGES + 2 * NB + 1 <= 28, "barriers fit their 256 bytes");
   static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
   // instruction descriptor: D = f32, A = B = bf16, both K-major, N >> 3, M >> 4
   static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_BN >> 3) << 17) |
@@ -275,11 +279,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
   const uint32_t bars = base + C::STAGES * C::STAGE_BYTES;
   auto full_bar = [&](int s) { return bars + 8u * s; };
   auto empty_bar = [&](int s) { return bars + 8u * (C::STAGES + s); };
-  auto ready_bar = [&](int l) { return bars + 8u * (2 * C::STAGES + l); };
-  auto drained_bar = [&](int l) { return bars + 8u * (2 * C::STAGES + LV + l); };
-  const uint32_t done_bar = bars + 8u * (2 * C::STAGES + 2 * LV);
+  auto ready_bar = [&](int b) { return bars + 8u * (2 * C::STAGES + b); };          // buffer b holds a chunk
+  auto drained_bar = [&](int b) { return bars + 8u * (2 * C::STAGES + C::NB + b); };  // buffer b is free
+  const uint32_t done_bar = bars + 8u * (2 * C::STAGES + 2 * C::NB);
   uint32_t* tmem_slot =
-      reinterpret_cast<uint32_t*>(gbase + C::STAGES * C::STAGE_BYTES + 8 * (2 * C::STAGES + 2 * LV + 1));
+      reinterpret_cast<uint32_t*>(gbase + C::STAGES * C::STAGE_BYTES + 8 * (2 * C::STAGES + 2 * C::NB + 1));
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   volatile int* skip_flag = reinterpret_cast<volatile int*>(tmem_slot + 2);
   volatile int never = 0;  // abort flag of the clean-up waits, which must not stop early
@@ -290,9 +294,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
       mbar_init(full_bar(s), 1);
       mbar_init(empty_bar(s), 1);
     }
-    for (int l = 0; l < LV; ++l) {
-      mbar_init(ready_bar(l), 1);
-      mbar_init(drained_bar(l), OZ_EPI_WARPS);
+    for (int b = 0; b < C::NB; ++b) {
+      mbar_init(ready_bar(b), 1);
+      mbar_init(drained_bar(b), OZ_EPI_WARPS);
     }
     mbar_init(done_bar, 1);
     *abort_flag = 0;
@@ -339,8 +343,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
         if (last_round[s] >= 0) mbar_wait(full_bar(s), (uint32_t)last_round[s] & 1u, &never);
     }
   } else if (warp == 1 && lane == 0) {
-    // ---------------- MMA issuer: level l accumulates into TMEM columns [64 l, 64 l + 64)
+    // ---------------- MMA issuer: TMEM buffer b = columns [64 b, 64 b + 64)
     bool ok = true;
+    uint32_t used = 0, par = 0;  // per buffer: used before; parity of its uses so far
     for (int it = 0; it < nk && ok; ++it) {
       const int s = it % C::STAGES;
       const uint32_t ph = (uint32_t)(it / C::STAGES) & 1u;
@@ -353,26 +358,34 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
       const uint32_t st = base + s * C::STAGE_BYTES;
       const uint64_t adesc0 = smem_desc_sw(st, C::SBO, C::LAYOUT);
       const uint64_t bdesc0 = smem_desc_sw(st + LV * C::A_BYTES, C::SBO, C::LAYOUT);
-      // level l's exact chunks are staggered by l stages, so at most one level changes chunk at a
-      // stage and its drain overlaps the other levels' MMAs; chunk k of level l covers stages
-      // [k CK - l, (k + 1) CK - l).  The MMAs run A-slice-major (pa outer, pb inner), so the A
-      // collector keeps slice pa for all its partners and A is read from shared memory once.
+      // Level l's exact chunks are staggered by l stages (chunk k covers stages [k CK - l,
+      // (k + 1) CK - l)), so at most one level starts a chunk per stage, and chunk k of level l
+      // accumulates in TMEM buffer (l + k) mod NB.  That buffer last held chunk k - 1 of level
+      // l + 1, which ended two stages earlier: its drain has a full stage to finish.  The MMAs run
+      // A-slice-major (pa outer, pb inner), so the A collector keeps slice pa for all its partners
+      // and A is read from shared memory once per stage.
 #pragma unroll
       for (int pa = 0; pa < LV && ok; ++pa) {
 #pragma unroll
         for (int pb = 0; pb < LV - pa; ++pb) {
           const int l = pa + pb;
-          const int pos = (it + l) % C::CK;
-          const bool first = pos == 0 || it == 0;
-          if (pa == 0 && first && it > 0 &&
-              !mbar_wait(drained_bar(l), (uint32_t)((it + l) / C::CK - 1) & 1u, abort_flag, a.wait_ns)) {
-            *abort_flag = 1;
-            status_set(a.e.status, KF_ERR_TIMEOUT, a.e.step, 13);
-            ok = false;
-            break;
+          const int k = (it + l) / C::CK;
+          const int b = (l + k) % C::NB;
+          const bool first = (it + l) % C::CK == 0 || it == 0;
+          if (pa == 0 && first) {
+            if ((used >> b) & 1u) {
+              if (!mbar_wait(drained_bar(b), ((par >> b) & 1u) ^ 1u, abort_flag, a.wait_ns)) {
+                *abort_flag = 1;
+                status_set(a.e.status, KF_ERR_TIMEOUT, a.e.step, 13);
+                ok = false;
+                break;
+              }
+              asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            }
+            used |= 1u << b;
+            par ^= 1u << b;
           }
-          if (pa == 0) asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t dacc = tmem + (uint32_t)(l * OZ_BN);
+          const uint32_t dacc = tmem + (uint32_t)(b * OZ_BN);
           const uint32_t acc = (first && pa == 0) ? 0u : 1u;
           // the start-address field (bits 0-13, 16-byte units) absorbs the in-stage offsets
           const uint64_t ad = adesc0 + (uint64_t)((pa * C::A_BYTES) >> 4);
@@ -391,7 +404,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
       if (!ok) break;
 #pragma unroll
       for (int l = 0; l < LV; ++l)
-        if ((it + l) % C::CK == C::CK - 1 || it == nk - 1) mma_commit(ready_bar(l));
+        if ((it + l) % C::CK == C::CK - 1 || it == nk - 1) mma_commit(ready_bar((l + (it + l) / C::CK) % C::NB));
       if (ok) mma_commit(empty_bar(s));
     }
   } else if (warp >= 2) {
@@ -404,11 +417,15 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
     bool ok = true;
     // drain events in the MMA issuer's order: at stage it, the level whose staggered chunk ends
     // there; at the last stage, every level
+    uint32_t rpar = 0;  // per buffer: parity of its drains so far
     for (int it = 0; it < nk && ok; ++it) {
       const bool final_stage = it == nk - 1;
       const int lone = (C::CK - 1 - it % C::CK);  // the level whose chunk ends at stage it
       for (int l = final_stage ? 0 : lone; l < (final_stage ? LV : min(lone + 1, LV)); ++l) {
-        if (!mbar_wait(ready_bar(l), (uint32_t)((it + l) / C::CK) & 1u, abort_flag, a.wait_ns)) {
+        const int b = (l + (it + l) / C::CK) % C::NB;
+        const uint32_t ph = (rpar >> b) & 1u;
+        rpar ^= 1u << b;
+        if (!mbar_wait(ready_bar(b), ph, abort_flag, a.wait_ns)) {
           if (!*abort_flag) {
             *abort_flag = 1;
             status_set(a.e.status, KF_ERR_TIMEOUT, a.e.step, 14);
@@ -417,8 +434,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(l * OZ_BN + h * 16);
-        const uint32_t dbar = drained_bar(l);
+        const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * OZ_BN + h * 16);
+        const uint32_t dbar = drained_bar(b);
         // compile-time level, so the shifts are constants and the conversions 32-bit
         switch (l) {
           case 0: oz_drain<0, LV>(taddr, dbar, lane, hi, lo); break;
