@@ -7,7 +7,7 @@ over all T steps and the backward smoother over T - 1 steps.  The metric is
 KF+FIS timesteps/s (T per epoch), with algorithmic TFLOP/s beside it.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-               [--prec mixed|fp32|fp64] [--solve fp32|fp64]
+               [--prec mixed|fp32|fp64] [--solve fp64tc|fp64mean|fp32|fp64]
 
 Multi-GPU (torchrun): every rank runs its own independent epoch (replicas;
 the recursion in t is sequential and the epochs share nothing), the timed
@@ -140,9 +140,13 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp32", "fp64"])
-    ap.add_argument("--solve", default="fp32", choices=["fp32", "fp64", "fp64tc", "fp64mean"],
-                    help="smoother-gain solve: float32 class, float64 on the CUDA cores, or float64-accurate on "
-                         "the tensor cores (float32-class factor + Newton steps with exact-slice residuals)")
+    ap.add_argument("--solve", default="fp64tc", choices=["fp32", "fp64", "fp64tc", "fp64mean"],
+                    help="smoother-gain solve: fp64tc = float64-accurate on the tensor cores (float32-class "
+                         "factor + Newton steps with exact-slice residuals; the workload's float64 smoother "
+                         "solve), fp64mean = the smoothed mean's solve refined to float64 accuracy, fp32 = "
+                         "float32 class, fp64 = float64 on the CUDA cores")
+    ap.add_argument("--no-solve-variants", action="store_true",
+                    help="skip the whole-epoch rates of the other tensor-core solve modes")
     ap.add_argument("--T", type=int, default=T_STEPS, help="time steps per epoch (the workload uses 300)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-plain", action="store_true")
@@ -315,7 +319,7 @@ def main():
         dist.barrier()
     elapsed = ev0.elapsed_time(ev1) / 1e3
     launches = B.kf_plan_launch_count(plan.handle) - launches0
-    prof = {c: B.kf_plan_profile_read(plan.handle, c) for c in range(9)}
+    prof = {c: B.kf_plan_profile_read(plan.handle, c) for c in range(10)}
     B.kf_plan_profile(plan.handle, False)
     if world > 1:
         t = torch.tensor([elapsed], device="cuda", dtype=torch.float64)
@@ -387,12 +391,37 @@ def main():
     if roof_solve["achieved"] is not None:
         roof_solve["frac"] = roof_solve["achieved"] / roof_solve["peak"]
     names = {0: "filter_update", 1: "innovation", 2: "smoother_gemm", 3: "smoother_solve", 4: "predict",
-             5: "solve_factor", 6: "solve_gain", 7: "smoother_gemm_kernel", 8: "solve_refine"}
+             5: "solve_factor", 6: "solve_gain", 7: "smoother_gemm_kernel", 8: "solve_refine",
+             9: "refine_exact_kernel"}
+    roof_smoother = roof
+    # With the float64-accurate solve the dominant kernel is the exact-slice residual product
+    # (I - P X_0 with 5 slice levels = 15 bf16 products, then I - P X_1 with 7 levels = 28), each
+    # launch timed alone (class 9).  Its tensor work is the bf16 products it issues; the float64
+    # product it delivers (2 N^3 per launch) is reported beside it against the float64 peak.
+    if prof[9][0] > 0 and prof[9][1] > prof[7][1]:
+        n_x, ms_x = prof[9]
+        pairs_per_step, launches_per_step = 15 + 28, 2
+        steps_x = n_x / launches_per_step
+        issued = pairs_per_step * 2 * N ** 3 * steps_x
+        t_x = ms_x / 1e3
+        roof = {"bound": "tensor", "kernel": "oz_gemm_kernel<5>, oz_gemm_kernel<7> (exact-slice I - P X)",
+                "achieved": issued / t_x / 1e12, "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s",
+                "peak_source": peak_src,
+                "peak_note": "bf16_tflops_sustained (measured): the products are bf16 slice products",
+                "traffic": None, "launches": n_x, "avg_launch_ms": ms_x / max(n_x, 1),
+                "work_per_launch": f"(15 or 28) x 2 N^3 bf16 flops, N = {N} (levels 5 and 7)",
+                "fp64_equivalent_tflops": launches_per_step * 2 * N ** 3 * steps_x / t_x / 1e12,
+                "fp64_equivalent_note": "2 N^3 float64-accurate flops per launch, vs 1.25 TFLOP/s nominal "
+                                        "float64 of this GPU",
+                "mma_shape_ceiling": 0.67,
+                "mma_shape_note": "128 x 64 x 16 MMAs (one 64-column TMEM accumulator per slice level) run "
+                                  "at 67% of the bf16 rate (probe: 48 cycles vs 64 for 128 x 128 x 16)"}
+        roof["frac"] = roof["achieved"] / roof["peak"]
 
     line = {"metric": METRIC, "value": value, "unit": "timesteps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None,
-            "dtype": {"mixed": "bf16x3+f32", "fp32": "f32", "fp64": "f64"}[args.prec] +
+            "dtype": {"mixed": "bf16x3+f32+f64", "fp32": "f32", "fp64": "f64"}[args.prec] +
                      ("" if args.prec == "fp64" else f"/solve-{args.solve}"),
             "data": "synthetic",
             "config": {"workload": prob.name, "N": N, "m": m, "T": T, "F": "identity", "precision": args.prec,
@@ -407,6 +436,7 @@ def main():
             "tflops_equivalent_note": "standard operation count of KF + FIS (Cholesky + two N-RHS solves "
                                       "for the gain), as if the path executed it",
             "roofline": roof,
+            "roofline_smoother": roof_smoother,
             "roofline_solve": roof_solve,
             "gpu_launches": launches,
             "clocks": clocks,
@@ -420,6 +450,8 @@ def main():
         line["serve"] = serving_sample(args, B, synth)
     if rank == 0 and world == 1 and not args.no_fp64_plain and args.prec != "fp64":
         line["fp64_plain"] = fp64_plain_prefix(prob, B, solver, synth, torch)
+    if rank == 0 and world == 1 and not args.no_solve_variants and args.prec == "mixed":
+        line["solve_variants"] = solve_variants(args, B, solver, prob, torch)
     if rank == 0 and world == 1 and args.config1_prefix > 0:
         line["config1"] = config1_sample(args, B, solver, synth, torch)
     if rank == 0 and world == 1 and not args.no_config2_mesh:
@@ -463,6 +495,22 @@ def batched_sample(args, B, synth):
     summ["epochs_per_s"] = summ["completed"] / summ["wall_s"] if summ["wall_s"] > 0 else 0.0
     summ["sample"] = f"{len(probs)} epochs, 8 concurrent plans on separate streams"
     return summ
+
+
+def solve_variants(args, B, solver, prob, torch):
+    """The same workload (whole epochs, inputs resident) with the other tensor-core solve modes, so
+    the price of each precision contract of the smoother-gain solve is visible beside the headline."""
+    out = {}
+    modes = {"fp64tc": B.KF_SOLVE_FP64_TC, "fp64mean": B.KF_SOLVE_FP64_MEAN, "fp32": B.KF_SOLVE_FP32}
+    for name, sv in modes.items():
+        if name == args.solve:
+            continue
+        r, dt, _ = _epoch_rate(prob, B, solver, torch, reps=2, prec=B.KF_PREC_MIXED_BF16X3, solve_prec=sv,
+                               joseph_every=16)
+        out[name] = {"value": r, "unit": "timesteps/s", "s_per_epoch": dt}
+    out["note"] = ("fp64tc: every J_t float64-accurate; fp64mean: the smoothed mean's solve float64-accurate, "
+                   "J_t inside the split-bf16 covariance product float32-class; fp32: float32-class solve")
+    return out
 
 
 def _epoch_rate(prob, B, solver, torch, reps=1, **kw):

@@ -213,7 +213,9 @@ typedef enum {
                              /* kernel launches alone (one mark per launch)        */
   KF_KC_SOLVE_REFINE = 8,    /* inside SOLVE_GAIN, KF_SOLVE_FP64_TC: the Newton      */
                              /* refinement of the inverse of P_{t+1|t}             */
-  KF_KC_COUNT = 9
+  KF_KC_REFINE_EXACT_KERNEL = 9, /* inside SOLVE_REFINE: the exact-slice residual  */
+                             /* kernel launches alone (I - P X_0, then I - P X_1)  */
+  KF_KC_COUNT = 10
 } kf_kernel_class;
 kf_status kf_plan_profile(kf_plan_t p, int32_t enable);
 kf_status kf_plan_profile_read(kf_plan_t p, int32_t cls, int64_t* launches,

@@ -24,7 +24,8 @@ KF_PREC_FP64, KF_PREC_FP32, KF_PREC_MIXED_BF16X3 = 0, 1, 2
 KF_SOLVE_FP64, KF_SOLVE_FP32, KF_SOLVE_FP64_TC, KF_SOLVE_FP64_MEAN = 0, 1, 2, 3
 KF_COV_SCALAR, KF_COV_DIAG, KF_COV_DENSE = 0, 1, 2
 KF_KC_FILTER_UPDATE, KF_KC_INNOVATION, KF_KC_SMOOTH_GEMM, KF_KC_SMOOTH_SOLVE, KF_KC_PREDICT, \
-    KF_KC_SOLVE_FACTOR, KF_KC_SOLVE_GAIN, KF_KC_SMOOTH_GEMM_KERNEL, KF_KC_SOLVE_REFINE = range(9)
+    KF_KC_SOLVE_FACTOR, KF_KC_SOLVE_GAIN, KF_KC_SMOOTH_GEMM_KERNEL, KF_KC_SOLVE_REFINE, \
+    KF_KC_REFINE_EXACT_KERNEL = range(10)
 
 
 class KfDesc(ctypes.Structure):

@@ -571,9 +571,9 @@ kf_status launch_oz(cudaStream_t s, const OzSlices& A, const OzSlices& B, int M,
   a.wait_ns = g_tc_wait_ns.load();
   KF_CUDA_TRY(smem_limit_per_device((const void*)oz_gemm_kernel<LV, BK>, (int)C::SMEM));
   const int64_t tiles = ceil_div(M, OZ_BM) * ceil_div(N, OZ_BN);
-  if (g_tc_timer) g_tc_timer->before(s);
+  if (g_oz_timer) g_oz_timer->before(s);
   oz_gemm_kernel<LV, BK><<<dim3((unsigned)tiles, (unsigned)splits), OZ_THREADS, C::SMEM, s>>>(maps, a);
-  if (g_tc_timer) g_tc_timer->after(s);
+  if (g_oz_timer) g_oz_timer->after(s);
   note_launch();
   KF_TRY(launch_check("oz_gemm"));
   if (splits > 1) {
@@ -586,6 +586,8 @@ kf_status launch_oz(cudaStream_t s, const OzSlices& A, const OzSlices& B, int M,
 }
 
 }  // namespace
+
+thread_local TcLaunchTimer* g_oz_timer = nullptr;
 
 uint64_t oz_slice_bytes(int64_t rows, int64_t cols, int S) {
   const uint64_t rp = round_up(std::max<int64_t>(rows, 1), OZ_ROW_PAD), ldk = round_up(std::max<int64_t>(cols, 1), 64);

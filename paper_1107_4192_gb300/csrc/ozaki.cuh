@@ -79,6 +79,10 @@ struct OzEpilogue {
   int step = 0;
 };
 
+// Optional event timing of the exact-slice kernel launches alone (installed by a plan while it
+// profiles the smoother-gain refinement).
+extern thread_local TcLaunchTimer* g_oz_timer;
+
 // C = A B^T for A (M x K) and B (N x K) given by their slices, keeping the
 // slice levels l < levels (4 to 7; both operands need at least `levels`
 // slices).  K <= 2^20.  splits > 1 divides K among that many CTAs per output

@@ -254,16 +254,19 @@ struct Prof {
   }
 };
 
-// Times the tensor-core kernel launches alone while installed (class cls).
+// Times the tensor-core kernel launches alone while installed (class cls): the split-bf16 kernel,
+// or with exact = true the exact-slice kernel.
 struct KernelTimer : TcLaunchTimer {
   kf_plan_s* p;
   int cls;
+  bool exact;
   cudaEvent_t a = nullptr;
-  KernelTimer(kf_plan_s* plan, int c) : p(plan), cls(c) {
-    if (p->prof) g_tc_timer = this;
+  KernelTimer(kf_plan_s* plan, int c, bool ex = false) : p(plan), cls(c), exact(ex) {
+    if (p->prof) (exact ? g_oz_timer : g_tc_timer) = this;
   }
   ~KernelTimer() override {
     if (g_tc_timer == this) g_tc_timer = nullptr;
+    if (g_oz_timer == this) g_oz_timer = nullptr;
   }
   cudaEvent_t take() {
     if (!p->pool.empty()) {
@@ -284,6 +287,11 @@ struct KernelTimer : TcLaunchTimer {
     cudaEventRecord(b, s);
     p->marks.push_back({cls, a, b});
   }
+};
+
+// Times the exact-slice kernel launches alone while installed (class cls).
+struct OzKernelTimer : KernelTimer {
+  OzKernelTimer(kf_plan_s* plan, int c) : KernelTimer(plan, c, true) {}
 };
 
 // ------------------------------------------------------------ GEMM dispatch
@@ -834,6 +842,7 @@ kf_status run_smoother(kf_plan_s* p, double* x_smooth, double* diagP_smooth, dou
         // float64-accurate P_{t+1|t}^{-1} from the float32-class factor; J_t in float64 (mean) and
         // float32 (covariance products)
         Prof pr(p, KF_KC_SOLVE_REFINE);
+        OzKernelTimer kt(p, KF_KC_REFINE_EXACT_KERNEL);
         const bool ident = p->d.f_kind == KF_F_IDENTITY && p->d.q_kind != KF_COV_DENSE;
         KF_TRY(refine_inverse_tc(s, p->tc, (int)N, (const float*)Pn, ldN, p->Wi, ldN, p->rb, p->d.q_kind,
                                  ident ? p->Q : nullptr, p->J64, (float*)Jb, ldN, p->rb.X0, ldN, p->status,
