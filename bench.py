@@ -565,7 +565,7 @@ def config2_mesh_sample(args, B, solver, synth, torch):
     rule = 2 * prob.N * prob.N * prob.T * 4
     ck = int(round(np.sqrt(prob.T))) if rule > budget else 0
     solve = {"fp32": B.KF_SOLVE_FP32, "fp64": B.KF_SOLVE_FP64, "fp64tc": B.KF_SOLVE_FP64_TC,
-             "fp64mean": B.KF_SOLVE_FP32}[args.solve]  # the mean-only refinement needs F = I or dense F
+             "fp64mean": B.KF_SOLVE_FP64_MEAN}[args.solve]
     r, dt, ck_used = _epoch_rate(prob, B, solver, torch, prec=B.KF_PREC_MIXED_BF16X3, solve_prec=solve,
                                  joseph_every=16, mem_budget_bytes=budget, checkpoint_every=ck)
     return {"workload": prob.name, "value": r, "unit": "timesteps/s", "s": dt, "checkpoint_every": ck_used,

@@ -74,14 +74,17 @@ typedef enum {
                              /* P_{t+1|t} refined by two Newton steps whose residuals */
                              /* I - P X are exact-slice products (kfx_spd_inverse    */
                              /* mode 2); J_t in float64 for the smoothed mean        */
-  KF_SOLVE_FP64_MEAN = 3     /* needs KF_PREC_MIXED_BF16X3 and F = I or dense: the   */
-                             /* smoothed mean's solve y = P_{t+1|t}^{-1} d (eqn 12)  */
-                             /* refined to float64 accuracy (float64 residuals       */
-                             /* d - P y, the float32-class inverse as preconditioner, */
-                             /* three steps), x_{t|T} = x_{t|t} + P_{t|t} F^T y;     */
-                             /* J_t inside the split-bf16 covariance product of      */
-                             /* eqn 13 from the float32-class inverse                */
+  KF_SOLVE_FP64_MEAN = 3     /* needs KF_PREC_MIXED_BF16X3: the smoothed mean's solve */
+                             /* y = P_{t+1|t}^{-1} d (eqn 12) refined to float64     */
+                             /* accuracy (float64 residuals d - P y, the float32-    */
+                             /* class inverse as preconditioner, three steps),       */
+                             /* x_{t|T} = x_{t|t} + P_{t|t} F^T y; J_t inside the     */
+                             /* split-bf16 covariance product of eqn 13 from the     */
+                             /* float32-class inverse                                */
 } kf_solve_precision;
+/* In KF_PREC_MIXED_BF16X3 every float64 solve (FP64, FP64_TC, FP64_MEAN) inverts the same
+ * P_{t+1|t} = F P_{t|t} F^T + Q, formed in float64 from the float32 stored P_{t|t}, and their
+ * smoothed means agree to float64 rounding times the conditioning. */
 
 typedef enum { KF_COV_SCALAR = 0, KF_COV_DIAG = 1, KF_COV_DENSE = 2 } kf_cov_kind;
 

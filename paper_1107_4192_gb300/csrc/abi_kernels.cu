@@ -172,7 +172,7 @@ kf_status kfx_spd_inverse(int32_t mode, int64_t n, const float* A, int64_t lda, 
   } else if (st == KF_OK) {
     RefineBufs rb;
     refine_layout(rb, rmem, n, ld);
-    st = refine_inverse_tc(s, sc, (int)n, A, lda, W, ld, rb, 0, nullptr, nullptr, nullptr, 0,
+    st = refine_inverse_tc(s, sc, (int)n, A, 0, lda, W, ld, rb, 0, nullptr, nullptr, nullptr, 0,
                            X, ldx, status, 1);
   }
   int h[ST_WORDS] = {0, 0, 0, 0};

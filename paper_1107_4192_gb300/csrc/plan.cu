@@ -47,6 +47,9 @@ struct kf_plan_s {
   bool refine = false;    // KF_SOLVE_FP64_TC: float64-accurate inverse of P_{t+1|t}
   bool mean_refine = false;  // KF_SOLVE_FP64_MEAN: float64-accurate solve of the smoothed mean
   float* X0f = nullptr;      // W^T W (KF_SOLVE_FP64_MEAN)
+  // Mixed path with a float64 smoother solve (KF_SOLVE_FP64, _TC, _MEAN): P_{t+1|t} formed in
+  // float64 from the float32 store, and F P_{t|t} (non-identity F) for the mean's P_{t|t} F^T y.
+  double *Pn64 = nullptr, *FP64 = nullptr;
   double *ysol = nullptr, *rsol = nullptr, *wsol = nullptr;  // its vectors
   int smooth_slices = 2;  // bf16 planes per operand in the smoother products (mixed mode)
   size_t b = 8, sb = 8;   // bytes per bulk / solve element
@@ -138,6 +141,8 @@ Sizes sizes_for(const kf_desc* d) {
   if (d->prec == KF_PREC_MIXED_BF16X3 && z.sb == 4) w += z.slot;         // Wi
   if (d->solve_prec == KF_SOLVE_FP64_TC) w += refine_bytes(N, ldN) + N * ldN * 8;  // refinement, J in float64
   if (d->solve_prec == KF_SOLVE_FP64_MEAN) w += z.slot + 3 * N * 8;                 // W^T W, vectors
+  if (d->prec == KF_PREC_MIXED_BF16X3 && d->solve_prec != KF_SOLVE_FP32)
+    w += N * ldN * 8 * (d->f_kind != KF_F_IDENTITY ? 2 : 1) + 3 * N * 8;          // P_{t+1|t}, F P, vectors
   if (d->prec == KF_PREC_MIXED_BF16X3) {
     // exact-slice filter: U, L^{-1}, L^{-T}, [K V], [V K], S partials, slices
     w += m * ldN * 8 + 2 * m * m * 8 + (d->joseph_every > 0 ? 4 * N * ldm * 8 : 0) + kOzSplitsS * m * m * 8 + 8;
@@ -167,7 +172,6 @@ kf_status validate(const kf_desc* d) {
   if (d->solve_prec < 0 || d->solve_prec > 3) return KF_ERR_ARG;
   if ((d->solve_prec == KF_SOLVE_FP64_TC || d->solve_prec == KF_SOLVE_FP64_MEAN) && d->prec != KF_PREC_MIXED_BF16X3)
     return KF_ERR_ARG;
-  if (d->solve_prec == KF_SOLVE_FP64_MEAN && d->f_kind == KF_F_CSR) return KF_ERR_UNSUPPORTED;
   if (d->q_kind < 0 || d->q_kind > 2 || d->r_kind < 0 || d->r_kind > 2) return KF_ERR_ARG;
   if (d->joseph_every < 0 || d->checkpoint_every < 0) return KF_ERR_ARG;
   if (d->split_terms != 0 && d->split_terms != 3 && d->split_terms != 6) return KF_ERR_ARG;
@@ -732,6 +736,33 @@ kf_status run_filter(kf_plan_s* p, const double* Y, const double* x0, const doub
   return read_status(p, fail_step);
 }
 
+// P_{t+1|t} = F P_{t|t} F^T + Q in float64 from the float32 stored P_{t|t} (Pn64), keeping F P_{t|t}
+// in FP64 for non-identity F: the matrix every float64 smoother solve of the mixed path inverts,
+// so that all of them compute the same J_t = P_{t|t} F^T P_{t+1|t}^{-1} (eqn 11).
+kf_status predict_store64(kf_plan_s* p, const float* Pt) {
+  cudaStream_t s = p->s;
+  const int64_t N = p->N, ldN = p->ldN;
+  if (p->d.f_kind == KF_F_IDENTITY)
+    return add_cov<double, float>(s, p->Pn64, ldN, Pt, ldN, N, p->d.q_kind, p->Q);
+  KF_TRY((copy2d<double, float>(s, p->W64, ldN, Pt, ldN, N, N)));  // float64 copy of P_{t|t}
+  if (p->d.f_kind == KF_F_CSR)
+    return spmm_fpft<double>(s, N, p->Frp, p->Fcol, p->F, p->W64, ldN, p->FP64, ldN, p->Pn64, ldN, p->d.q_kind,
+                             p->Q);
+  GemmParams<double> g;  // F P, then (F P) F^T + Q
+  g.M = (int)N; g.N = (int)N; g.K = (int)N;
+  g.A = p->F; g.lda = N;
+  g.B = p->W64; g.ldb = ldN;
+  g.out = p->FP64; g.ldo = ldN;
+  KF_TRY(gemm_simt<double>(s, false, g));
+  GemmParams<double> h;
+  h.M = (int)N; h.N = (int)N; h.K = (int)N;
+  h.A = p->FP64; h.lda = ldN;
+  h.B = p->F; h.ldb = N;
+  h.out2 = p->Pn64; h.ldo2 = ldN;
+  h.q_kind = p->d.q_kind; h.q = p->Q; h.ldq = N;
+  return gemm_simt<double>(s, true, h);
+}
+
 // Cholesky + inverse of the working P_{t+1|t} (in Lb) for smoother step `step`,
 // replayed from a CUDA graph after the first step has run eagerly.
 kf_status chol_inverse_step(kf_plan_s* p, float* Lb, int step) {
@@ -786,6 +817,8 @@ kf_status run_smoother(kf_plan_s* p, double* x_smooth, double* diagP_smooth, dou
   V* Lb = (V*)p->Lb;
   V* Jb = (V*)p->Jb;
   B* Jm = sizeof(V) == sizeof(B) ? (B*)p->Jb : (B*)p->Jm;
+  // a float64 solve in the mixed path: one float64 definition of P_{t+1|t} and of the mean (above)
+  const bool fp64sv = p->bulk == BULK_BF16X3 && (sizeof(V) == 8 || p->refine || p->mean_refine);
   // t = T: smoothed = filtered
   KF_CUDA_TRY(cudaMemcpyAsync(p->xs + T * N, p->xfilt + T * N, N * 8, cudaMemcpyDeviceToDevice, s));
   const B* PT;
@@ -811,8 +844,16 @@ kf_status run_smoother(kf_plan_s* p, double* x_smooth, double* diagP_smooth, dou
     const B* Pt;
     {
       Prof pr(p, KF_KC_SMOOTH_SOLVE);
-      // P_{t+1|t} = L L^T
-      KF_TRY((copy2d<V, B>(s, Lb, ldN, Pn, ldN, N, N)));
+      KF_TRY(get_P<B>(p, t, &Pt));
+      // P_{t+1|t} = L L^T: the bulk prediction, or for a float64 solve of the mixed path the
+      // float64 prediction from the stored P_{t|t} (the float32 factor of the tensor-core solves is
+      // then its float32 rounding, a preconditioner the refinement corrects)
+      if (fp64sv) {
+        KF_TRY(predict_store64(p, (const float*)Pt));
+        KF_TRY((copy2d<V, double>(s, Lb, ldN, p->Pn64, ldN, N, N)));
+      } else {
+        KF_TRY((copy2d<V, B>(s, Lb, ldN, Pn, ldN, N, N)));
+      }
       const bool tc_solve = p->bulk == BULK_BF16X3 && sizeof(V) == 4;
       {
         Prof pf(p, KF_KC_SOLVE_FACTOR);
@@ -821,7 +862,6 @@ kf_status run_smoother(kf_plan_s* p, double* x_smooth, double* diagP_smooth, dou
         else
           KF_TRY(potrf<V>(s, Lb, ldN, (int)N, (V*)p->Ldinv, nbs, p->status, (int)(t + 1)));
       }
-      KF_TRY(get_P<B>(p, t, &Pt));
       // J_t = P_{t|t} F^T P_{t+1|t}^{-1}
       const B* Bm = Pt;
       if (p->d.f_kind == KF_F_CSR) {
@@ -844,14 +884,15 @@ kf_status run_smoother(kf_plan_s* p, double* x_smooth, double* diagP_smooth, dou
         Prof pr(p, KF_KC_SOLVE_REFINE);
         OzKernelTimer kt(p, KF_KC_REFINE_EXACT_KERNEL);
         const bool ident = p->d.f_kind == KF_F_IDENTITY && p->d.q_kind != KF_COV_DENSE;
-        KF_TRY(refine_inverse_tc(s, p->tc, (int)N, (const float*)Pn, ldN, p->Wi, ldN, p->rb, p->d.q_kind,
+        KF_TRY(refine_inverse_tc(s, p->tc, (int)N, p->Pn64, 1, ldN, p->Wi, ldN, p->rb, p->d.q_kind,
                                  ident ? p->Q : nullptr, p->J64, (float*)Jb, ldN, p->rb.X0, ldN, p->status,
                                  (int)(t + 1)));
         if (!ident) {
-          GemmParams<double> g;  // J = (P_{t|t} F^T) X, X = P_{t+1|t}^{-1} symmetric (its rows are its columns)
+          // J = (P_{t|t} F^T) X for the covariance products (X = P_{t+1|t}^{-1} symmetric: its rows are
+          // its columns); the mean uses X itself below
+          GemmParams<float> g;
           g.M = (int)N; g.N = (int)N; g.K = (int)N;
-          g.out = p->J64; g.ldo = ldN;
-          g.outf = (float*)Jb; g.ldof = ldN;
+          g.out = (float*)Jb; g.ldo = ldN;
           g.status = p->status;
           KF_TRY(tc_gemm_ops(s, p->tc, TcOperand{Bm, ldN, 0, 0}, TcOperand{p->rb.X0, ldN, 1, 0}, g, 3));
         }
@@ -893,26 +934,35 @@ kf_status run_smoother(kf_plan_s* p, double* x_smooth, double* diagP_smooth, dou
     }
     // x_{t|T} = x_{t|t} + J_t (x_{t+1|T} - x_{t+1|t})
     KF_TRY(vsub(s, N, p->xs + (t + 1) * N, p->xpred + (t + 1) * N, p->dx));
-    if (p->refine) {
-      KF_TRY(gemv<double>(s, N, N, p->J64, ldN, p->dx, p->xfilt + t * N, 1.0, p->xs + t * N));
-    } else if (p->mean_refine) {
-      // y = P_{t+1|t}^{-1} dx by iterative refinement: float64 residuals r = dx - P y against the
-      // float32 P_{t+1|t}, corrections y += X0 r with the float32-class inverse (each step shrinks
-      // the error by |I - X0 P| ~ 1e-5); then x_{t|T} = x_{t|t} + P_{t|t} F^T y
-      const float* Pp = (const float*)Pn;
-      KF_TRY(gemv<float>(s, N, N, p->X0f, ldN, p->dx, nullptr, 1.0, p->ysol));
-      for (int k = 0; k < 3; ++k) {
-        KF_TRY(gemv_f64acc(s, N, N, Pp, ldN, p->ysol, p->dx, -1.0, p->rsol));
-        KF_TRY(gemv<float>(s, N, N, p->X0f, ldN, p->rsol, p->ysol, 1.0, p->ysol));
-      }
-      const double* w = p->ysol;
-      if (p->d.f_kind == KF_F_DENSE) {  // w = F^T y
-        KF_TRY(gemv_t(s, N, N, p->F, N, p->ysol, nullptr, 1.0, p->wsol));
-        w = p->wsol;
-      }
-      KF_TRY(gemv_f64acc(s, N, N, (const float*)Pt, ldN, w, p->xfilt + t * N, 1.0, p->xs + t * N));
-    } else
+    if (!fp64sv) {
       KF_TRY(gemv<V>(s, N, N, Jb, ldN, p->dx, p->xfilt + t * N, 1.0, p->xs + t * N));
+    } else if (p->refine && p->d.f_kind == KF_F_IDENTITY && p->d.q_kind != KF_COV_DENSE) {
+      KF_TRY(gemv<double>(s, N, N, p->J64, ldN, p->dx, p->xfilt + t * N, 1.0, p->xs + t * N));
+    } else {
+      // x_{t|T} = x_{t|t} + P_{t|t} F^T y with y = P_{t+1|t}^{-1} dx to float64 accuracy
+      double* y = p->ysol;
+      if (sizeof(V) == 8) {  // float64 Cholesky factor: two triangular solves of the row vector dx
+        KF_CUDA_TRY(cudaMemcpyAsync(y, p->dx, N * 8, cudaMemcpyDeviceToDevice, s));
+        KF_TRY(trsm_right<double>(s, true, 1, (int)N, (const double*)Lb, ldN, (const double*)p->Ldinv, nbs, y, N,
+                                  p->status));
+        KF_TRY(trsm_right<double>(s, false, 1, (int)N, (const double*)Lb, ldN, (const double*)p->Ldinv, nbs, y, N,
+                                  p->status));
+      } else if (p->refine) {  // the float64-accurate inverse
+        KF_TRY(gemv<double>(s, N, N, p->rb.X0, ldN, p->dx, nullptr, 1.0, y));
+      } else {
+        // iterative refinement: float64 residuals r = dx - P y, corrections y += X0 r with the
+        // float32-class inverse (each step shrinks the error by |I - X0 P| ~ 1e-5)
+        KF_TRY(gemv<float>(s, N, N, p->X0f, ldN, p->dx, nullptr, 1.0, y));
+        for (int k = 0; k < 3; ++k) {
+          KF_TRY(gemv<double>(s, N, N, p->Pn64, ldN, y, p->dx, -1.0, p->rsol));
+          KF_TRY(gemv<float>(s, N, N, p->X0f, ldN, p->rsol, y, 1.0, y));
+        }
+      }
+      if (p->d.f_kind == KF_F_IDENTITY)
+        KF_TRY(gemv_f64acc(s, N, N, (const float*)Pt, ldN, y, p->xfilt + t * N, 1.0, p->xs + t * N));
+      else  // P_{t|t} F^T y = (F P_{t|t})^T y
+        KF_TRY(gemv_t(s, N, N, p->FP64, ldN, y, p->xfilt + t * N, 1.0, p->xs + t * N));
+    }
     if ((void*)Jm != (void*)Jb) KF_TRY((copy2d<B, V>(s, Jm, ldN, Jb, ldN, N, N)));
     {
       Prof pr(p, KF_KC_SMOOTH_GEMM);
@@ -1054,8 +1104,10 @@ kf_status kf_plan(kf_plan_t* out, const kf_desc* d) {
   A(&p->Ldinv, round_up(N, nbs) * nbs * sb);
   if (sb != b) A(&p->Jm, p->slot);
   if (p->bulk == BULK_BF16X3 && sb == 4) A(&p->Wi, p->slot);
-  if (p->mean_refine) {
-    A(&p->X0f, p->slot);
+  if (p->mean_refine) A(&p->X0f, p->slot);
+  if (p->bulk == BULK_BF16X3 && d->solve_prec != KF_SOLVE_FP32) {
+    A(&p->Pn64, N * ldN * 8);
+    if (d->f_kind != KF_F_IDENTITY) A(&p->FP64, N * ldN * 8);
     A(&p->ysol, N * 8);
     A(&p->rsol, N * 8);
     A(&p->wsol, N * 8);

@@ -192,7 +192,7 @@ void refine_layout(RefineBufs& rb, void* mem, int64_t n, int64_t ld) {
   oz_slice_layout(rb.Xs, p + 3 * mat + round_up((int64_t)oz_slice_bytes(n, n, 7), 256), n, n, 7);
 }
 
-kf_status refine_inverse_tc(cudaStream_t s, TcScratch& sc, int n, const float* P, int64_t ldp, const float* W,
+kf_status refine_inverse_tc(cudaStream_t s, TcScratch& sc, int n, const void* P, int p_f64, int64_t ldp, const float* W,
                             int64_t ldw, RefineBufs& rb, int q_kind, const double* gain_q, double* J64, float* Jf,
                             int64_t ldj, double* X2, int64_t ldx, int* status, int step) {
   if (gain_q && q_kind != 0 && q_kind != 1) return KF_ERR_ARG;
@@ -207,7 +207,7 @@ kf_status refine_inverse_tc(cudaStream_t s, TcScratch& sc, int n, const float* P
     g.status = status;
     KF_TRY(tc_gemm_ops(s, sc, TcOperand{W, ldw, 0, 1}, TcOperand{W, ldw, 0, 1}, g, 3));
   }
-  KF_TRY(oz_slice(s, P, ldp, 0, n, n, 7, rb.Ps));
+  KF_TRY(oz_slice(s, P, ldp, p_f64, n, n, 7, rb.Ps));
   const double* X = rb.X0;
   for (int k = 0; k < 2; ++k) {
     // R_k = I - P X_k  (X_k symmetric: its rows are the product's columns)

@@ -34,7 +34,7 @@ struct RefineBufs {
 uint64_t refine_bytes(int64_t n, int64_t ld);
 void refine_layout(RefineBufs& rb, void* mem, int64_t n, int64_t ld);
 
-// Inverse of the symmetric positive definite P (float32, n x n) to float64
+// Inverse of the symmetric positive definite P (float32, or float64 when p_f64; n x n) to float64
 // accuracy, from W = L^{-1} of its float32-class factor (chol_inverse_tc):
 //   X0 = W^T W;   R_k = I - P X_k;   X_{k+1} = X_k + X_k R_k   (k = 0, 1)
 // (Newton's iteration for the inverse, quadratically convergent from the
@@ -45,7 +45,7 @@ void refine_layout(RefineBufs& rb, void* mem, int64_t n, int64_t ld);
 //  - gain_q != NULL (F = I, Q = q I or diagonal): J = I - Q X_2 into J64
 //    (float64) and Jf (float32), X_2 itself never stored;
 //  - gain_q == NULL: X_2 into X2 (float64, n x ldx).
-kf_status refine_inverse_tc(cudaStream_t s, TcScratch& sc, int n, const float* P, int64_t ldp, const float* W,
+kf_status refine_inverse_tc(cudaStream_t s, TcScratch& sc, int n, const void* P, int p_f64, int64_t ldp, const float* W,
                             int64_t ldw, RefineBufs& rb, int q_kind, const double* gain_q, double* J64, float* Jf,
                             int64_t ldj, double* X2, int64_t ldx, int* status, int step);
 

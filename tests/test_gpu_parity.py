@@ -170,33 +170,26 @@ def test_mixed_long_epoch_T300(long_epoch, solve):
 
 
 @pytest.mark.parametrize("solve", [B.KF_SOLVE_FP64_TC, B.KF_SOLVE_FP64_MEAN])
-@pytest.mark.parametrize("dense", [False, True])
-def test_fp64_accurate_solves_match_the_cuda_core_solve(solve, dense):
+@pytest.mark.parametrize("fkind", ["identity", "mesh", "dense"])
+def test_fp64_accurate_solves_match_the_cuda_core_solve(solve, fkind):
     """With the same mixed filter (float64-class, so filtered means and stored P_{t|t} are the
-    same launch sequence), the smoothed means of the float64-accurate tensor-core solves equal
-    those of the float64 CUDA-core solve (Cholesky + two triangular solves) to float64 rounding
-    times the conditioning, far below the float32-class solve's difference."""
-    prob = synth.dense_dynamics_problem(384, 40, 12, seed=5) if dense else synth.mesh_problem(
-        600, 64, 12, seed=7, identity_F=True)
-    kw = dict(prec=B.KF_PREC_MIXED_BF16X3, joseph_every=4, dense_F=dense)
+    same launch sequence) every float64 solve inverts the same float64 P_{t+1|t} = F P_{t|t} F^T + Q:
+    the smoothed means of the float64-accurate tensor-core solves equal those of the float64
+    CUDA-core solve (Cholesky + two triangular solves) to float64 rounding times the conditioning,
+    far below the float32-class solve's difference."""
+    prob = {"dense": lambda: synth.dense_dynamics_problem(384, 40, 12, seed=5),
+            "mesh": lambda: synth.mesh_problem(324, 40, 12, seed=6),
+            "identity": lambda: synth.mesh_problem(600, 64, 12, seed=7, identity_F=True)}[fkind]()
+    kw = dict(prec=B.KF_PREC_MIXED_BF16X3, joseph_every=4, dense_F=fkind == "dense")
     ref = solver.run(prob, solve_prec=B.KF_SOLVE_FP64, **kw)
     out = solver.run(prob, solve_prec=solve, **kw)
     f32 = solver.run(prob, solve_prec=B.KF_SOLVE_FP32, **kw)
     assert np.array_equal(out["x_filt"], ref["x_filt"])
     e = rel_err_per_step(out["x_smooth"], ref["x_smooth"])
     e32 = rel_err_per_step(f32["x_smooth"], ref["x_smooth"])
-    print(f"solve {solve} dense {dense}: smoothed means vs float64 solve {e:.2e} (float32-class solve {e32:.2e})")
+    print(f"solve {solve} F {fkind}: smoothed means vs float64 solve {e:.2e} (float32-class solve {e32:.2e})")
     assert e <= 1e-10
     assert rel_err_elementwise(out["diagP_smooth"], ref["diagP_smooth"]) <= TOL_DIAG32
-
-
-def test_fp64_mean_solve_rejects_compressed_row_F():
-    prob = synth.mesh_problem(64, 8, 3, seed=1)
-    d = solver.upload(prob)
-    with pytest.raises(B.KfError) as e:
-        solver.Plan.for_inputs(d, prob.N, prob.m, prob.T, prec=B.KF_PREC_MIXED_BF16X3,
-                               solve_prec=B.KF_SOLVE_FP64_MEAN)
-    assert e.value.status == B.KF_ERR_UNSUPPORTED
 
 
 def test_full_smoothed_covariance_output():
