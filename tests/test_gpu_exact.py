@@ -127,7 +127,7 @@ def spd32(n, cond, seed):
     return A.astype(np.float32)
 
 
-@pytest.mark.parametrize("n,cond", [(257, 100.0), (1024, 100.0), (2048, 100.0), (1024, 1000.0)])
+@pytest.mark.parametrize("n,cond", [(257, 100.0), (1024, 100.0), (2048, 100.0), (4096, 100.0), (1024, 1000.0)])
 def test_refined_inverse_is_float64_accurate(n, cond):
     A = spd32(n, cond, n)
     dA = torch.from_numpy(A).cuda()
