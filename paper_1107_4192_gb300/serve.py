@@ -43,10 +43,11 @@ from . import solver
 class Request:
     rid: int
     arrival_s: float
-    problem: object                     # synth.Problem (inputs arrive with the request)
+    problem: object                     # synth.Problem, or a callable returning one (built when admitted)
     prec: int = B.KF_PREC_MIXED_BF16X3
-    solve_prec: int = B.KF_SOLVE_FP32
+    solve_prec: int = B.KF_SOLVE_FP64_MEAN
     joseph_every: int = 16
+    shape: Optional[tuple] = None       # (N, m, T, f_kind) when problem is a callable
 
 
 @dataclass
@@ -88,11 +89,62 @@ def input_bytes(prob) -> int:
     return b
 
 
+@dataclass
+class LazyProblem:
+    """A request's shape, with its synthetic inputs built only when it is admitted (the inputs of
+    a served request arrive with it; building them is the stand-in for receiving them)."""
+    N: int
+    m: int
+    T: int
+    identity_F: bool
+    seed: int
+    q_kind: int = 0
+    r_kind: int = 1
+
+    @property
+    def f_kind(self):
+        return B.KF_F_IDENTITY if self.identity_F else B.KF_F_CSR
+
+    @property
+    def nnz(self):
+        return 0 if self.identity_F else _mesh_nnz(self.N)
+
+    @property
+    def F(self):
+        return None if self.identity_F else _NnzOnly(self.nnz)
+
+    def build(self):
+        from . import synth
+        return synth.mesh_problem(self.N, self.m, self.T, seed=self.seed, identity_F=self.identity_F)
+
+
+@dataclass
+class _NnzOnly:
+    nnz: int
+
+
+_NNZ = {}
+
+
+def _mesh_nnz(N):
+    if N not in _NNZ:
+        from . import synth
+        _NNZ[N] = synth.mesh_coupling(synth.hemisphere_mesh(N)).nnz
+    return _NNZ[N]
+
+
+def _kinds(prob):
+    """(f_kind, nnz, q_kind, r_kind) of a problem, without building its arrays."""
+    if prob.F is None:
+        return B.KF_F_IDENTITY, 0, prob.q_kind, prob.r_kind
+    return B.KF_F_CSR, prob.F.nnz, prob.q_kind, prob.r_kind
+
+
 def plan_bytes(prob, req: Request, budget: int):
     """(status, bytes, checkpoint_every) of the plan this request would allocate within `budget`."""
-    h = solver.host_inputs(prob)
-    d = B.make_desc(prob.N, prob.m, prob.T, h["f_kind"], req.prec, req.solve_prec, h["q_kind"], h["r_kind"],
-                    req.joseph_every, h["f_nnz"], budget, 0, 0, 0)
+    f_kind, nnz, q_kind, r_kind = _kinds(prob)
+    d = B.make_desc(prob.N, prob.m, prob.T, f_kind, req.prec, req.solve_prec, q_kind, r_kind,
+                    req.joseph_every, nnz, budget, 0, 0, 0)
     st, w, s, c = B.kf_plan_footprint(d)
     return st, w + s, c
 
@@ -131,6 +183,8 @@ class Server:
         import torch
         prob = req.problem
         try:
+            if isinstance(prob, LazyProblem):
+                prob = prob.build()
             stream = torch.cuda.Stream()
             with torch.cuda.stream(stream):
                 d = solver.upload(prob, self.device)
@@ -238,3 +292,50 @@ def run_batch(problems, max_slots: int = 8, budget_bytes: int = 160 * 10 ** 9, p
     res = server.run(reqs)
     wall = time.perf_counter() - t0
     return res, summarize(res, wall)
+
+
+def main(argv=None):
+    """Replays the seeded Poisson request stream of the serving workload (20 req/s; N in {1024, 2048,
+    5124, 8196}, m = 306, T ~ U{50..400}; F = I or mesh coupling by request parity) through the
+    continuous-batching server with admission by footprint against the budget, and writes the
+    summary (p50/p99 latency, timesteps/s, recompute count) as JSON."""
+    import argparse
+    import json
+
+    import torch
+
+    from . import build, synth
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--requests", type=int, default=2000)
+    ap.add_argument("--rate", type=float, default=20.0)
+    ap.add_argument("--slots", type=int, default=4)
+    ap.add_argument("--budget-gb", type=float, default=160.0)
+    ap.add_argument("--out", default="")
+    args = ap.parse_args(argv)
+    build.build()
+    B.lib()
+    torch.cuda.init()
+    arrivals = synth.serving_arrivals(args.requests, args.rate, seed=4)
+    reqs = [Request(i, t, LazyProblem(N, m, T, identity_F=(i % 2 == 0), seed=4000 + i))
+            for i, (t, N, m, T) in enumerate(arrivals)]
+    t0 = time.perf_counter()
+    res = Server(int(args.budget_gb * 1e9), max_slots=args.slots).run(reqs)
+    wall = time.perf_counter() - t0
+    out = summarize(res, wall)
+    by_n = {}
+    for r in res:
+        if r.status == "ok":
+            by_n.setdefault(r.N, []).append(r.latency_s)
+    out["p50_latency_s_by_N"] = {int(n): float(np.percentile(v, 50)) for n, v in sorted(by_n.items())}
+    out["workload"] = (f"{args.requests} requests, Poisson arrivals at {args.rate} req/s over "
+                       f"{arrivals[-1][0]:.1f} s, {args.slots} slots, budget {args.budget_gb} GB, mixed path "
+                       f"(split-bf16 products, float64-class filter, float64-accurate smoothed-mean solve)")
+    line = json.dumps(out)
+    print(line, flush=True)
+    if args.out:
+        with open(args.out, "w") as f:
+            f.write(line + "\n")
+
+
+if __name__ == "__main__":
+    main()

@@ -132,3 +132,15 @@ def test_arena_backs_plans_without_allocation(built):
         B.kf_arena_release()
     for k in ref:
         assert np.array_equal(ref[k], out[k]), k
+
+
+@pytest.mark.parametrize("identity_F", [True, False])
+def test_lazy_problem_charges_like_the_built_one(built, identity_F):
+    lazy = serve.LazyProblem(600, 40, 30, identity_F=identity_F, seed=7)
+    prob = lazy.build()
+    assert (prob.N, prob.m, prob.T, prob.q_kind, prob.r_kind) == (600, 40, 30, lazy.q_kind, lazy.r_kind)
+    assert (prob.F is None) == identity_F and (identity_F or prob.F.nnz == lazy.nnz)
+    assert serve.input_bytes(lazy) == serve.input_bytes(prob)
+    req = serve.Request(0, 0.0, lazy)
+    for budget in (0, serve.input_bytes(prob) + 2 * 600 * 600 * 4 * 8):
+        assert serve.plan_bytes(lazy, req, budget) == serve.plan_bytes(prob, req, budget)
