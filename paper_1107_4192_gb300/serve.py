@@ -43,11 +43,14 @@ from . import solver
 class Request:
     rid: int
     arrival_s: float
-    problem: object                     # synth.Problem, or a callable returning one (built when admitted)
+    problem: object                     # synth.Problem, or a LazyProblem (built when admitted)
     prec: int = B.KF_PREC_MIXED_BF16X3
-    solve_prec: int = B.KF_SOLVE_FP64_MEAN
+    solve_prec: Optional[int] = None    # None: float64-accurate smoothed mean on the mixed path, else float32
     joseph_every: int = 16
-    shape: Optional[tuple] = None       # (N, m, T, f_kind) when problem is a callable
+
+    def __post_init__(self):
+        if self.solve_prec is None:
+            self.solve_prec = B.KF_SOLVE_FP64_MEAN if self.prec == B.KF_PREC_MIXED_BF16X3 else B.KF_SOLVE_FP32
 
 
 @dataclass

@@ -144,3 +144,10 @@ def test_lazy_problem_charges_like_the_built_one(built, identity_F):
     req = serve.Request(0, 0.0, lazy)
     for budget in (0, serve.input_bytes(prob) + 2 * 600 * 600 * 4 * 8):
         assert serve.plan_bytes(lazy, req, budget) == serve.plan_bytes(prob, req, budget)
+
+
+def test_request_solve_default_follows_the_precision():
+    p = synth.random_walk_problem(64, 8, 3, seed=1)
+    assert serve.Request(0, 0.0, p).solve_prec == B.KF_SOLVE_FP64_MEAN
+    assert serve.Request(0, 0.0, p, prec=B.KF_PREC_FP64).solve_prec == B.KF_SOLVE_FP32
+    assert serve.Request(0, 0.0, p, solve_prec=B.KF_SOLVE_FP64_TC).solve_prec == B.KF_SOLVE_FP64_TC
