@@ -7,21 +7,23 @@
 // x (the float64 units of this GPU would make float64 slicing the slow part).
 //
 // Product (oz_gemm_kernel): one 128 x 64 output tile per CTA, 18 warps.
-//   warp 0  one lane issues the TMA loads (64-byte swizzle) of all slices of a
-//           32-wide k-slice of A and B into a shared-memory stage;
-//   warp 1  allocates TMEM (one 128 x 64 float32 accumulator per slice level),
-//           one lane issues, per stage and level, the MMAs of the level's
-//           slice pairs into that level's accumulator, and after the last
-//           k-slice of a 128-wide chunk commits each level to its "ready"
-//           barrier; a level's first MMA of the next chunk waits until the
-//           epilogue has drained it;
+//   warp 0  one lane issues the TMA loads (32-byte swizzle) of all slices of a
+//           16-wide k-slice of A and B into a shared-memory stage;
+//   warp 1  allocates TMEM (LV + 1 buffers of 128 x 64 float32, rotating among
+//           the levels so a level's drain overlaps the MMAs); the whole warp
+//           runs the issue loop (warp-uniform arithmetic) and one elected lane
+//           issues, per stage, the MMAs of every slice pair: per A slice, its
+//           partner levels in runs of up to four whose buffers are adjacent,
+//           one MMA of N = 64 x run each; after the last k-slice of a level's
+//           128-wide chunk it commits the level's buffer to its "ready"
+//           barrier, and a level's next chunk starts (overwriting) in a buffer
+//           the epilogue has drained;
 //   warps 2-17 per chunk and level, read the accumulator (an exact integer
 //           below 2^24), convert it to an integer and add it into 64-bit
 //           fixed-point accumulators in registers (levels 0-2 and levels 3..
 //           in two of them); at the end scale by the row and column exponents
 //           and apply the float64 epilogue.
-// The drain of level l overlaps the MMAs of the later levels.  Every
-// pipeline wait is bounded (kernel argument, as in the split-bf16 kernel).
+// Every pipeline wait is bounded (kernel argument, as in the split-bf16 kernel).
 #include "ozaki.cuh"
 #include "tc_ptx.cuh"
 
@@ -58,15 +60,14 @@ struct OzCfg {
   // so the buffer a level leaves is drained while the MMAs continue in the spare one
   static constexpr int NB = LV + 1;
   static_assert(NB * OZ_BN <= 512, "one TMEM accumulator per level plus a spare");
-  static_assert(LV < CK, "one level changes chunk per stage");
+  static_assert(LV < CK && CK == 8, "one level changes chunk per stage; eight stage patterns");
   // a level has at most LV slice pairs whose products are below 2^14 in magnitude, so one
   // chunk of OZ_KC values of k sums to an integer below 2^24: exact in float32
   static_assert(LV * OZ_KC * 16384 <= (1 << 24), "exact chunk");
   static_assert(2 * STAGES + 2 * NB + 1 <= 28, "barriers fit their 256 bytes");
   static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
-  // instruction descriptor: D = f32, A = B = bf16, both K-major, N >> 3, M >> 4
-  static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_BN >> 3) << 17) |
-                                    ((uint32_t)(OZ_BM >> 4) << 24);
+  // instruction descriptor: D = f32, A = B = bf16, both K-major, M >> 4; N >> 3 at bit 17 per MMA
+  static constexpr uint32_t IDESC_M = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_BM >> 4) << 24);
 };
 
 struct OzMaps {
@@ -236,7 +237,7 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const T* X, int64_t ld, i
 }
 
 // One level's drain by an epilogue warp: read its 16 accumulator columns (exact integers below
-// 2^24), hand the accumulator back to the MMA issuer, and add the values into the 64-bit fixed-point
+// 2^24), hand the buffer back to the MMA issuer, and add the values into the 64-bit fixed-point
 // sums (levels 0-2 in units of level 2, levels 3.. in units of level LV-1).
 template <int L, int LV>
 __device__ __forceinline__ void oz_drain(uint32_t taddr, uint32_t dbar, int lane, long long (&hi)[16],
@@ -254,6 +255,47 @@ __device__ __forceinline__ void oz_drain(uint32_t taddr, uint32_t dbar, int lane
         hi[j] += v << (8 * (2 - L));
       else
         lo[j] += v << (8 * (LV - 1 - L));
+    }
+  }
+}
+
+// The MMAs of one pipeline stage with r = stage mod CK.  Level l's exact chunks are staggered by l
+// stages and chunk k of level l accumulates in TMEM buffer (l + k) mod NB, so at this stage level l
+// sits in buffer (l + [l >= CK - r] + cm) mod NB, cm = (stage / CK) mod NB.  Per A slice pa, its
+// partner levels pa .. LV-1 go in runs of up to four levels, split at the level CK - r that has
+// moved on (fixed by r, so the runs and all shared-memory offsets are compile-time): one MMA with
+// N = 64 x run takes the adjacent B slices pb .. pb+run-1 into the run's adjacent accumulators; a
+// run whose buffers pass the last one (known from cm at run time) is issued as two MMAs.  The level
+// LS that starts a chunk at this stage gets its own MMA at pa = 0, the chunk's first, which
+// overwrites the accumulator instead of adding to it (at the first stage every level starts, and
+// all of pa = 0's MMAs overwrite).
+template <int LV, int R>
+__device__ __forceinline__ void oz_issue_stage(bool leader, uint32_t tmem, uint64_t adesc0, uint64_t bdesc0, int cm,
+                                               bool first_stage) {
+  using C = OzCfg<LV, kOzBK>;
+  constexpr int LS = R == 0 ? 0 : C::CK - R;
+#pragma unroll
+  for (int pa = 0; pa < LV; ++pa) {
+    int l0 = pa;
+#pragma unroll
+    for (int l = pa + 1; l <= LV; ++l) {
+      if (l == LV || l - l0 == 4 || l == C::CK - R || (pa == 0 && LS < LV && l == LS + 1)) {
+        const int run = l - l0;
+        const uint32_t acc = (pa == 0 && (first_stage || l0 == LS)) ? 0u : 1u;
+        int b = l0 + (l0 >= C::CK - R ? 1 : 0) + cm;
+        if (b >= C::NB) b -= C::NB;
+        const int first = min(run, C::NB - b);
+        // the start-address field (bits 0-13, 16-byte units) absorbs the in-stage offsets
+        const uint64_t ad = adesc0 + (uint64_t)((pa * C::A_BYTES) >> 4);
+        const uint64_t bd = bdesc0 + (uint64_t)(((l0 - pa) * C::B_BYTES) >> 4);
+        if (leader) {
+          mma_bf16(tmem + (uint32_t)(b * OZ_BN), ad, bd, C::IDESC_M | ((uint32_t)(first * OZ_BN) >> 3 << 17), acc);
+          if (first < run)
+            mma_bf16(tmem, ad, bd + (uint64_t)((first * C::B_BYTES) >> 4),
+                     C::IDESC_M | ((uint32_t)((run - first) * OZ_BN) >> 3 << 17), acc);
+        }
+        l0 = l;
+      }
     }
   }
 }
@@ -314,6 +356,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
   const uint32_t tmem = *tmem_slot;
   const bool skip = *skip_flag != 0 || nk <= 0;
   bool mma_issued = false;
+  bool leader = false;  // the MMA warp's issuing lane: it issues every MMA and every commit
 
   if (skip) {
     // an earlier kernel failed: do nothing but release TMEM below
@@ -342,70 +385,77 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
       for (int s = 0; s < C::STAGES; ++s)
         if (last_round[s] >= 0) mbar_wait(full_bar(s), (uint32_t)last_round[s] & 1u, &never);
     }
-  } else if (warp == 1 && lane == 0) {
-    // ---------------- MMA issuer: TMEM buffer b = columns [64 b, 64 b + 64)
+  } else if (warp == 1) {
+    // ---------------- MMA issuer: the whole warp runs the loop, so the stage, buffer and descriptor
+    // arithmetic is warp-uniform; one elected lane issues.  TMEM buffer b = columns [64 b, 64 b + 64).
+    // Level l's exact chunks are staggered by l stages (chunk k covers stages [k CK - l,
+    // (k + 1) CK - l)), so at most one level starts a chunk per stage, and chunk k of level l
+    // accumulates in buffer (l + k) mod NB.  That buffer last held chunk k - 1 of level l + 1, which
+    // ended two stages earlier: its drain has a full stage to finish.
+    leader = elect_one();
     bool ok = true;
     uint32_t used = 0, par = 0;  // per buffer: used before; parity of its uses so far
     for (int it = 0; it < nk && ok; ++it) {
       const int s = it % C::STAGES;
       const uint32_t ph = (uint32_t)(it / C::STAGES) & 1u;
-      if (!mbar_wait(full_bar(s), ph, abort_flag, a.wait_ns)) {
-        *abort_flag = 1;
-        status_set(a.e.status, KF_ERR_TIMEOUT, a.e.step, 12);
+      ok = __all_sync(0xffffffffu, mbar_wait(full_bar(s), ph, abort_flag, a.wait_ns));
+      if (!ok) {
+        if (lane == 0) {
+          *abort_flag = 1;
+          status_set(a.e.status, KF_ERR_TIMEOUT, a.e.step, 12);
+        }
         break;
+      }
+      const int ck = it / C::CK, r = it - ck * C::CK, cm = ck % C::NB;
+      auto buf = [&](int l) {  // buffer of level l at this stage
+        const int b = l + cm + (l >= C::CK - r ? 1 : 0);
+        return b >= C::NB ? b - C::NB : b;
+      };
+      // the one level that starts a chunk here ((it + l) % CK == 0; every level at the first
+      // stage, in fresh buffers) waits until its buffer has been drained
+      if (it == 0) {
+        used = par = (1u << LV) - 1u;
+      } else {
+        const int ls = r == 0 ? 0 : C::CK - r;
+        if (ls < LV) {
+          const int b = buf(ls);
+          if ((used >> b) & 1u) {
+            ok = __all_sync(0xffffffffu, mbar_wait(drained_bar(b), ((par >> b) & 1u) ^ 1u, abort_flag, a.wait_ns));
+            if (!ok) {
+              if (lane == 0) {
+                *abort_flag = 1;
+                status_set(a.e.status, KF_ERR_TIMEOUT, a.e.step, 13);
+              }
+              break;
+            }
+          }
+          used |= 1u << b;
+          par ^= 1u << b;
+        }
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t st = base + s * C::STAGE_BYTES;
       const uint64_t adesc0 = smem_desc_sw(st, C::SBO, C::LAYOUT);
       const uint64_t bdesc0 = smem_desc_sw(st + LV * C::A_BYTES, C::SBO, C::LAYOUT);
-      // Level l's exact chunks are staggered by l stages (chunk k covers stages [k CK - l,
-      // (k + 1) CK - l)), so at most one level starts a chunk per stage, and chunk k of level l
-      // accumulates in TMEM buffer (l + k) mod NB.  That buffer last held chunk k - 1 of level
-      // l + 1, which ended two stages earlier: its drain has a full stage to finish.  The MMAs run
-      // A-slice-major (pa outer, pb inner), so the A collector keeps slice pa for all its partners
-      // and A is read from shared memory once per stage.
-#pragma unroll
-      for (int pa = 0; pa < LV && ok; ++pa) {
-#pragma unroll
-        for (int pb = 0; pb < LV - pa; ++pb) {
-          const int l = pa + pb;
-          const int k = (it + l) / C::CK;
-          const int b = (l + k) % C::NB;
-          const bool first = (it + l) % C::CK == 0 || it == 0;
-          if (pa == 0 && first) {
-            if ((used >> b) & 1u) {
-              if (!mbar_wait(drained_bar(b), ((par >> b) & 1u) ^ 1u, abort_flag, a.wait_ns)) {
-                *abort_flag = 1;
-                status_set(a.e.status, KF_ERR_TIMEOUT, a.e.step, 13);
-                ok = false;
-                break;
-              }
-              asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            }
-            used |= 1u << b;
-            par ^= 1u << b;
-          }
-          const uint32_t dacc = tmem + (uint32_t)(b * OZ_BN);
-          const uint32_t acc = (first && pa == 0) ? 0u : 1u;
-          // the start-address field (bits 0-13, 16-byte units) absorbs the in-stage offsets
-          const uint64_t ad = adesc0 + (uint64_t)((pa * C::A_BYTES) >> 4);
-          const uint64_t bd = bdesc0 + (uint64_t)((pb * C::B_BYTES) >> 4);
-          if (LV - pa == 1)
-            mma_bf16_coll<kCollNone>(dacc, ad, bd, C::IDESC, acc);
-          else if (pb == 0)
-            mma_bf16_coll<kCollFill>(dacc, ad, bd, C::IDESC, acc);
-          else if (pb == LV - 1 - pa)
-            mma_bf16_coll<kCollLastUse>(dacc, ad, bd, C::IDESC, acc);
-          else
-            mma_bf16_coll<kCollUse>(dacc, ad, bd, C::IDESC, acc);
-        }
-        mma_issued = true;
+      switch (r) {
+        case 0: oz_issue_stage<LV, 0>(leader, tmem, adesc0, bdesc0, cm, it == 0); break;
+        case 1: oz_issue_stage<LV, 1>(leader, tmem, adesc0, bdesc0, cm, it == 0); break;
+        case 2: oz_issue_stage<LV, 2>(leader, tmem, adesc0, bdesc0, cm, it == 0); break;
+        case 3: oz_issue_stage<LV, 3>(leader, tmem, adesc0, bdesc0, cm, it == 0); break;
+        case 4: oz_issue_stage<LV, 4>(leader, tmem, adesc0, bdesc0, cm, it == 0); break;
+        case 5: oz_issue_stage<LV, 5>(leader, tmem, adesc0, bdesc0, cm, it == 0); break;
+        case 6: oz_issue_stage<LV, 6>(leader, tmem, adesc0, bdesc0, cm, it == 0); break;
+        default: oz_issue_stage<LV, 7>(leader, tmem, adesc0, bdesc0, cm, it == 0); break;
       }
-      if (!ok) break;
+      __syncwarp();
+      mma_issued = true;
+      if (leader) {
 #pragma unroll
-      for (int l = 0; l < LV; ++l)
-        if ((it + l) % C::CK == C::CK - 1 || it == nk - 1) mma_commit(ready_bar((l + (it + l) / C::CK) % C::NB));
-      if (ok) mma_commit(empty_bar(s));
+        for (int l = 0; l < LV; ++l)
+          if ((it + l) % C::CK == C::CK - 1 || it == nk - 1) mma_commit(ready_bar(buf(l)));
+        mma_commit(empty_bar(s));
+      }
+      __syncwarp();
     }
   } else if (warp >= 2) {
     // ---------------- epilogue: exact level sums into 64-bit fixed point, then scale and store
@@ -524,7 +574,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
     }
   }
   // every issued MMA must have finished before TMEM is freed
-  if (!skip && warp == 1 && lane == 0 && mma_issued) {
+  if (!skip && warp == 1 && leader && mma_issued) {
     mma_commit(done_bar);
     mbar_wait(done_bar, 0, &never);
   }

@@ -26,14 +26,16 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+// Suspending test of an mbarrier phase: a thread whose phase is not complete sleeps (issuing
+// nothing) until the phase completes or about suspend_ns nanoseconds pass.
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity, uint32_t suspend_ns) {
   uint32_t ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}\n"
       : "=r"(ok)
-      : "r"(bar), "r"(parity)
+      : "r"(bar), "r"(parity), "r"(suspend_ns)
       : "memory");
   return ok != 0;
 }
@@ -51,28 +53,25 @@ __device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity) {
 }
 
 // Bounded wait on an mbarrier phase; false on timeout or when another role
-// aborted.  Limits of 1 ms and more use the suspending try_wait and read the
-// clock every 64 polls; shorter limits poll without suspending and read the
-// clock after every poll, so the limit alone decides when the wait ends.
-static __device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, uint64_t limit_ns = WAIT_NS) {
+// aborted.  A phase that is already complete costs one test (the clock is
+// read only once the first test fails).  Limits of 1 ms and more sleep in the
+// suspending try_wait (20 us at a time, so waiting warps take no issue slots
+// from the working ones) and read the clock after each wake-up; shorter
+// limits poll without suspending and read the clock after every poll, so the
+// limit alone decides when the wait ends.
+constexpr uint32_t kMbarSuspendNs = 20000;
+static __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, uint64_t limit_ns = WAIT_NS) {
+  if (mbar_test_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer();
   if (limit_ns < 1000000ull) {
-    const uint64_t t0 = globaltimer();
     for (;;) {
       if (mbar_test_wait(bar, parity)) return true;
       if (*abort_flag || globaltimer() - t0 > limit_ns) return false;
     }
   }
-  uint64_t t0 = 0;
-  for (uint32_t it = 0;; ++it) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if ((it & 63u) == 63u) {
-      if (*abort_flag) return false;
-      const uint64_t now = globaltimer();
-      if (t0 == 0)
-        t0 = now;
-      else if (now - t0 > limit_ns)
-        return false;
-    }
+  for (;;) {
+    if (mbar_try_wait(bar, parity, kMbarSuspendNs)) return true;
+    if (*abort_flag || globaltimer() - t0 > limit_ns) return false;
   }
 }
 
@@ -169,6 +168,14 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
         "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// One lane of a converged warp (elect.sync over the full mask): the warp computes the MMA operands
+// as warp-uniform values and only the elected lane issues.
+__device__ __forceinline__ bool elect_one() {
+  uint32_t p = 0;
+  asm volatile("{\n\t.reg .pred P;\n\telect.sync _|P, 0xffffffff;\n\tselp.b32 %0, 1, 0, P;\n\t}\n" : "=r"(p));
+  return p != 0;
 }
 
 }  // namespace kfm
