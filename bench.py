@@ -413,9 +413,9 @@ def main():
                 "fp64_equivalent_tflops": launches_per_step * 2 * N ** 3 * steps_x / t_x / 1e12,
                 "fp64_equivalent_note": "2 N^3 float64-accurate flops per launch, vs 1.25 TFLOP/s nominal "
                                         "float64 of this GPU",
-                "mma_shape_ceiling": 0.67,
-                "mma_shape_note": "128 x 64 x 16 MMAs (one 64-column TMEM accumulator per slice level) run "
-                                  "at 67% of the bf16 rate (probe: 48 cycles vs 64 for 128 x 128 x 16)"}
+                "mma_shape_note": "per k-step and A slice, one 128 x (64 run) x 16 MMA per run of up to four "
+                                  "slice levels whose TMEM accumulators are adjacent (13.5 MMAs per k-step at "
+                                  "7 levels); probe: N = 64 runs at 67% of the bf16 rate, N = 256 at 100%"}
         roof["frac"] = roof["achieved"] / roof["peak"]
 
     line = {"metric": METRIC, "value": value, "unit": "timesteps/s", "n_gpus": world, "steps": args.steps,

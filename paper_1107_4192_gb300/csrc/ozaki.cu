@@ -7,8 +7,9 @@
 // x (the float64 units of this GPU would make float64 slicing the slow part).
 //
 // Product (oz_gemm_kernel): one 128 x 64 output tile per CTA, 18 warps.
-//   warp 0  one lane issues the TMA loads (32-byte swizzle) of all slices of a
-//           16-wide k-slice of A and B into a shared-memory stage;
+//   warp 0  one lane issues the TMA loads (64-byte swizzle) of all slices of a
+//           32-wide k-slice (two MMA k-steps) of A and B into a shared-memory
+//           stage;
 //   warp 1  allocates TMEM (LV + 1 buffers of 128 x 64 float32, rotating among
 //           the levels so a level's drain overlaps the MMAs); the whole warp
 //           runs the issue loop (warp-uniform arithmetic) and one elected lane
@@ -38,18 +39,20 @@ constexpr int OZ_EPI_WARPS = 16;  // 4 TMEM lane quadrants x 4 column quarters o
 constexpr int OZ_THREADS = 32 * (2 + OZ_EPI_WARPS);
 constexpr int OZ_GROUP = 8;     // row tiles per rasterisation group (operand reuse in L2)
 constexpr int OZ_ROW_PAD = 128;
-constexpr int kOzBK = 16;       // k per pipeline stage of the launched kernels
+constexpr int kOzBK = 32;       // k per pipeline stage of the launched kernels (two MMA k-steps)
 constexpr int kOzBadRow = 0x7fffffff;  // exponent marking a row that holds an infinity or NaN
 
 // LV slice levels; BK values of k per pipeline stage, one swizzled row of bf16 (16: 32-byte
-// swizzle, 32: 64-byte swizzle): smaller stages give a deeper pipeline for the same shared memory.
+// swizzle, one MMA k-step; 32: 64-byte swizzle, two k-steps, half the stages and wider TMA rows).
 template <int LV, int BK>
 struct OzCfg {
-  static_assert(BK == 16, "one 32-byte swizzle row per stage: one MMA k-step, so A-slice-major MMA order can use the A collector");
+  static_assert(BK == 16 || BK == 32, "one 32- or 64-byte swizzled row of bf16 per stage");
   static constexpr int SWZ = BK * 2;                         // swizzle width in bytes
   static constexpr uint32_t LAYOUT = BK == 16 ? kLayoutSw32 : kLayoutSw64;  // descriptor swizzle mode
   static constexpr uint32_t SBO = 8 * SWZ;                   // bytes between 8-row groups
+  static constexpr int KS = BK / 16;                         // MMA k-steps per stage
   static constexpr int CK = OZ_KC / BK;                      // stages per exact chunk
+  static constexpr int CKS = OZ_KC / 16;                     // k-steps per exact chunk
   static constexpr int A_BYTES = OZ_BM * BK * 2;
   static constexpr int B_BYTES = OZ_BN * BK * 2;
   static constexpr int STAGE_BYTES = LV * (A_BYTES + B_BYTES);
@@ -60,7 +63,7 @@ struct OzCfg {
   // so the buffer a level leaves is drained while the MMAs continue in the spare one
   static constexpr int NB = LV + 1;
   static_assert(NB * OZ_BN <= 512, "one TMEM accumulator per level plus a spare");
-  static_assert(LV < CK && CK == 8, "one level changes chunk per stage; eight stage patterns");
+  static_assert(LV < CKS && CKS == 8, "one level changes chunk per k-step; eight k-step patterns");
   // a level has at most LV slice pairs whose products are below 2^14 in magnitude, so one
   // chunk of OZ_KC values of k sums to an integer below 2^24: exact in float32
   static_assert(LV * OZ_KC * 16384 <= (1 << 24), "exact chunk");
@@ -259,30 +262,30 @@ __device__ __forceinline__ void oz_drain(uint32_t taddr, uint32_t dbar, int lane
   }
 }
 
-// The MMAs of one pipeline stage with r = stage mod CK.  Level l's exact chunks are staggered by l
-// stages and chunk k of level l accumulates in TMEM buffer (l + k) mod NB, so at this stage level l
-// sits in buffer (l + [l >= CK - r] + cm) mod NB, cm = (stage / CK) mod NB.  Per A slice pa, its
-// partner levels pa .. LV-1 go in runs of up to four levels, split at the level CK - r that has
+// The MMAs of one k-step t with r = t mod CKS.  Level l's exact chunks are staggered by l k-steps
+// and chunk k of level l accumulates in TMEM buffer (l + k) mod NB, so at this k-step level l sits
+// in buffer (l + [l >= CKS - r] + cm) mod NB, cm = (t / CKS) mod NB.  Per A slice pa, its
+// partner levels pa .. LV-1 go in runs of up to four levels, split at the level CKS - r that has
 // moved on (fixed by r, so the runs and all shared-memory offsets are compile-time): one MMA with
 // N = 64 x run takes the adjacent B slices pb .. pb+run-1 into the run's adjacent accumulators; a
 // run whose buffers pass the last one (known from cm at run time) is issued as two MMAs.  The level
-// LS that starts a chunk at this stage gets its own MMA at pa = 0, the chunk's first, which
-// overwrites the accumulator instead of adding to it (at the first stage every level starts, and
+// LS that starts a chunk at this k-step gets its own MMA at pa = 0, the chunk's first, which
+// overwrites the accumulator instead of adding to it (at the first k-step every level starts, and
 // all of pa = 0's MMAs overwrite).
-template <int LV, int R>
-__device__ __forceinline__ void oz_issue_stage(bool leader, uint32_t tmem, uint64_t adesc0, uint64_t bdesc0, int cm,
-                                               bool first_stage) {
-  using C = OzCfg<LV, kOzBK>;
-  constexpr int LS = R == 0 ? 0 : C::CK - R;
+template <int LV, int BK, int R>
+__device__ __forceinline__ void oz_issue_kstep(bool leader, uint32_t tmem, uint64_t adesc0, uint64_t bdesc0, int cm,
+                                               bool first_step) {
+  using C = OzCfg<LV, BK>;
+  constexpr int LS = R == 0 ? 0 : C::CKS - R;
 #pragma unroll
   for (int pa = 0; pa < LV; ++pa) {
     int l0 = pa;
 #pragma unroll
     for (int l = pa + 1; l <= LV; ++l) {
-      if (l == LV || l - l0 == 4 || l == C::CK - R || (pa == 0 && LS < LV && l == LS + 1)) {
+      if (l == LV || l - l0 == 4 || l == C::CKS - R || (pa == 0 && LS < LV && l == LS + 1)) {
         const int run = l - l0;
-        const uint32_t acc = (pa == 0 && (first_stage || l0 == LS)) ? 0u : 1u;
-        int b = l0 + (l0 >= C::CK - R ? 1 : 0) + cm;
+        const uint32_t acc = (pa == 0 && (first_step || l0 == LS)) ? 0u : 1u;
+        int b = l0 + (l0 >= C::CKS - R ? 1 : 0) + cm;
         if (b >= C::NB) b -= C::NB;
         const int first = min(run, C::NB - b);
         // the start-address field (bits 0-13, 16-byte units) absorbs the in-stage offsets
@@ -388,10 +391,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
   } else if (warp == 1) {
     // ---------------- MMA issuer: the whole warp runs the loop, so the stage, buffer and descriptor
     // arithmetic is warp-uniform; one elected lane issues.  TMEM buffer b = columns [64 b, 64 b + 64).
-    // Level l's exact chunks are staggered by l stages (chunk k covers stages [k CK - l,
-    // (k + 1) CK - l)), so at most one level starts a chunk per stage, and chunk k of level l
+    // Level l's exact chunks are staggered by l k-steps (chunk k covers k-steps [k CKS - l,
+    // (k + 1) CKS - l)), so at most one level starts a chunk per k-step, and chunk k of level l
     // accumulates in buffer (l + k) mod NB.  That buffer last held chunk k - 1 of level l + 1, which
-    // ended two stages earlier: its drain has a full stage to finish.
+    // ended two k-steps earlier: its drain has a full k-step of MMAs to finish.
     leader = elect_one();
     bool ok = true;
     uint32_t used = 0, par = 0;  // per buffer: used before; parity of its uses so far
@@ -406,55 +409,63 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
         }
         break;
       }
-      const int ck = it / C::CK, r = it - ck * C::CK, cm = ck % C::NB;
-      auto buf = [&](int l) {  // buffer of level l at this stage
-        const int b = l + cm + (l >= C::CK - r ? 1 : 0);
-        return b >= C::NB ? b - C::NB : b;
-      };
-      // the one level that starts a chunk here ((it + l) % CK == 0; every level at the first
-      // stage, in fresh buffers) waits until its buffer has been drained
-      if (it == 0) {
-        used = par = (1u << LV) - 1u;
-      } else {
-        const int ls = r == 0 ? 0 : C::CK - r;
-        if (ls < LV) {
-          const int b = buf(ls);
-          if ((used >> b) & 1u) {
-            ok = __all_sync(0xffffffffu, mbar_wait(drained_bar(b), ((par >> b) & 1u) ^ 1u, abort_flag, a.wait_ns));
-            if (!ok) {
-              if (lane == 0) {
-                *abort_flag = 1;
-                status_set(a.e.status, KF_ERR_TIMEOUT, a.e.step, 13);
-              }
-              break;
-            }
-          }
-          used |= 1u << b;
-          par ^= 1u << b;
-        }
-      }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t st = base + s * C::STAGE_BYTES;
-      const uint64_t adesc0 = smem_desc_sw(st, C::SBO, C::LAYOUT);
-      const uint64_t bdesc0 = smem_desc_sw(st + LV * C::A_BYTES, C::SBO, C::LAYOUT);
-      switch (r) {
-        case 0: oz_issue_stage<LV, 0>(leader, tmem, adesc0, bdesc0, cm, it == 0); break;
-        case 1: oz_issue_stage<LV, 1>(leader, tmem, adesc0, bdesc0, cm, it == 0); break;
-        case 2: oz_issue_stage<LV, 2>(leader, tmem, adesc0, bdesc0, cm, it == 0); break;
-        case 3: oz_issue_stage<LV, 3>(leader, tmem, adesc0, bdesc0, cm, it == 0); break;
-        case 4: oz_issue_stage<LV, 4>(leader, tmem, adesc0, bdesc0, cm, it == 0); break;
-        case 5: oz_issue_stage<LV, 5>(leader, tmem, adesc0, bdesc0, cm, it == 0); break;
-        case 6: oz_issue_stage<LV, 6>(leader, tmem, adesc0, bdesc0, cm, it == 0); break;
-        default: oz_issue_stage<LV, 7>(leader, tmem, adesc0, bdesc0, cm, it == 0); break;
-      }
-      __syncwarp();
-      mma_issued = true;
-      if (leader) {
+      const uint64_t adesc_s = smem_desc_sw(st, C::SBO, C::LAYOUT);
+      const uint64_t bdesc_s = smem_desc_sw(st + LV * C::A_BYTES, C::SBO, C::LAYOUT);
 #pragma unroll
-        for (int l = 0; l < LV; ++l)
-          if ((it + l) % C::CK == C::CK - 1 || it == nk - 1) mma_commit(ready_bar(buf(l)));
-        mma_commit(empty_bar(s));
+      for (int j = 0; j < C::KS; ++j) {
+        const int t = it * C::KS + j;  // k-step
+        const int ck = t / C::CKS, r = t - ck * C::CKS, cm = ck % C::NB;
+        auto buf = [&](int l) {  // buffer of level l at this k-step
+          const int b = l + cm + (l >= C::CKS - r ? 1 : 0);
+          return b >= C::NB ? b - C::NB : b;
+        };
+        // the one level that starts a chunk here ((t + l) % CKS == 0; every level at the first
+        // k-step, in fresh buffers) waits until its buffer has been drained
+        if (t == 0) {
+          used = par = (1u << LV) - 1u;
+        } else {
+          const int ls = r == 0 ? 0 : C::CKS - r;
+          if (ls < LV) {
+            const int b = buf(ls);
+            if ((used >> b) & 1u) {
+              ok = __all_sync(0xffffffffu, mbar_wait(drained_bar(b), ((par >> b) & 1u) ^ 1u, abort_flag, a.wait_ns));
+              if (!ok) {
+                if (lane == 0) {
+                  *abort_flag = 1;
+                  status_set(a.e.status, KF_ERR_TIMEOUT, a.e.step, 13);
+                }
+                break;
+              }
+            }
+            used |= 1u << b;
+            par ^= 1u << b;
+          }
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // k-step j reads the next 32 bytes of every swizzled row (start address in 16-byte units)
+        const uint64_t adesc0 = adesc_s + (uint64_t)(2 * j), bdesc0 = bdesc_s + (uint64_t)(2 * j);
+        switch (r) {
+          case 0: oz_issue_kstep<LV, BK, 0>(leader, tmem, adesc0, bdesc0, cm, t == 0); break;
+          case 1: oz_issue_kstep<LV, BK, 1>(leader, tmem, adesc0, bdesc0, cm, t == 0); break;
+          case 2: oz_issue_kstep<LV, BK, 2>(leader, tmem, adesc0, bdesc0, cm, t == 0); break;
+          case 3: oz_issue_kstep<LV, BK, 3>(leader, tmem, adesc0, bdesc0, cm, t == 0); break;
+          case 4: oz_issue_kstep<LV, BK, 4>(leader, tmem, adesc0, bdesc0, cm, t == 0); break;
+          case 5: oz_issue_kstep<LV, BK, 5>(leader, tmem, adesc0, bdesc0, cm, t == 0); break;
+          case 6: oz_issue_kstep<LV, BK, 6>(leader, tmem, adesc0, bdesc0, cm, t == 0); break;
+          default: oz_issue_kstep<LV, BK, 7>(leader, tmem, adesc0, bdesc0, cm, t == 0); break;
+        }
+        __syncwarp();
+        mma_issued = true;
+        if (leader) {  // the level whose chunk ends here (every level at the last k-step) is ready
+#pragma unroll
+          for (int l = 0; l < LV; ++l)
+            if ((t + l) % C::CKS == C::CKS - 1 || t == nk * C::KS - 1) mma_commit(ready_bar(buf(l)));
+        }
+        __syncwarp();
       }
+      if (!ok) break;
+      if (leader) mma_commit(empty_bar(s));
       __syncwarp();
     }
   } else if (warp >= 2) {
@@ -465,14 +476,15 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
 #pragma unroll
     for (int j = 0; j < 16; ++j) hi[j] = lo[j] = 0;
     bool ok = true;
-    // drain events in the MMA issuer's order: at stage it, the level whose staggered chunk ends
-    // there; at the last stage, every level
+    // drain events in the MMA issuer's order: at k-step t, the level whose staggered chunk ends
+    // there; at the last k-step, every level
     uint32_t rpar = 0;  // per buffer: parity of its drains so far
-    for (int it = 0; it < nk && ok; ++it) {
-      const bool final_stage = it == nk - 1;
-      const int lone = (C::CK - 1 - it % C::CK);  // the level whose chunk ends at stage it
-      for (int l = final_stage ? 0 : lone; l < (final_stage ? LV : min(lone + 1, LV)); ++l) {
-        const int b = (l + (it + l) / C::CK) % C::NB;
+    const int nks = nk * C::KS;
+    for (int t = 0; t < nks && ok; ++t) {
+      const bool final_step = t == nks - 1;
+      const int lone = (C::CKS - 1 - t % C::CKS);  // the level whose chunk ends at k-step t
+      for (int l = final_step ? 0 : lone; l < (final_step ? LV : min(lone + 1, LV)); ++l) {
+        const int b = (l + (t + l) / C::CKS) % C::NB;
         const uint32_t ph = (rpar >> b) & 1u;
         rpar ^= 1u << b;
         if (!mbar_wait(ready_bar(b), ph, abort_flag, a.wait_ns)) {
