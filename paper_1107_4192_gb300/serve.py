@@ -213,8 +213,12 @@ class Server:
             self._active -= 1
             self._cv.notify_all()
 
-    def run(self, requests: List[Request], time_scale: float = 1.0) -> List[Result]:
-        """Serves requests arriving at arrival_s * time_scale seconds after the start."""
+    def run(self, requests: List[Request], time_scale: float = 1.0, admit_until_s: Optional[float] = None,
+            progress=None, progress_every_s: float = 30.0) -> List[Result]:
+        """Serves requests arriving at arrival_s * time_scale seconds after the start.  With
+        admit_until_s, requests still waiting at that time are not admitted (status "not admitted")
+        and the run ends when the admitted ones finish; progress(results) is called about every
+        progress_every_s seconds."""
         reqs = sorted(requests, key=lambda r: r.arrival_s)
         results = {r.rid: Result(r.rid, r.problem.N, r.problem.m, r.problem.T, r.arrival_s * time_scale)
                    for r in reqs}
@@ -230,9 +234,20 @@ class Server:
         t0 = time.perf_counter()
         pending: List[Request] = []
         i = 0
+        last_progress = 0.0
         with self._cv:
             while i < len(reqs) or pending:
                 now = time.perf_counter() - t0
+                if progress is not None and now - last_progress >= progress_every_s:
+                    last_progress = now
+                    progress([results[r.rid] for r in reqs])
+                if admit_until_s is not None and now >= admit_until_s:
+                    for req in pending + reqs[i:]:
+                        res = results[req.rid]
+                        res.status = "not admitted: admission window closed"
+                        res.admitted_s = res.finished_s = now
+                    pending, i = [], len(reqs)
+                    break
                 while i < len(reqs) and reqs[i].arrival_s * time_scale <= now:
                     pending.append(reqs[i])
                     i += 1
@@ -277,6 +292,7 @@ def summarize(results: List[Result], wall_s: Optional[float] = None) -> dict:
                                               if ok else 0.0)
     return {"requests": len(results), "completed": len(ok),
             "rejected": sum(r.status.startswith("rejected") for r in results),
+            "not_admitted": sum(r.status.startswith("not admitted") for r in results),
             "errors": sum(r.status.startswith("error") for r in results),
             "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
             "mean_queue_s": float(np.mean([r.queue_s for r in ok])) if ok else 0.0,
@@ -314,6 +330,8 @@ def main(argv=None):
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--budget-gb", type=float, default=160.0)
     ap.add_argument("--out", default="")
+    ap.add_argument("--admit-window-s", type=float, default=None,
+                    help="admit no request after this many seconds (the rest are reported as not admitted)")
     args = ap.parse_args(argv)
     build.build()
     B.lib()
@@ -321,8 +339,18 @@ def main(argv=None):
     arrivals = synth.serving_arrivals(args.requests, args.rate, seed=4)
     reqs = [Request(i, t, LazyProblem(N, m, T, identity_F=(i % 2 == 0), seed=4000 + i))
             for i, (t, N, m, T) in enumerate(arrivals)]
+
+    def progress(results):
+        done = [r for r in results if r.finished_s > 0]
+        if args.out and done:
+            part = summarize(done, time.perf_counter() - t0)
+            part["finished_so_far"] = len(done)
+            with open(args.out + ".partial", "w") as f:
+                f.write(json.dumps(part) + "\n")
+
     t0 = time.perf_counter()
-    res = Server(int(args.budget_gb * 1e9), max_slots=args.slots).run(reqs)
+    res = Server(int(args.budget_gb * 1e9), max_slots=args.slots).run(reqs, admit_until_s=args.admit_window_s,
+                                                                        progress=progress)
     wall = time.perf_counter() - t0
     out = summarize(res, wall)
     by_n = {}
@@ -330,6 +358,8 @@ def main(argv=None):
         if r.status == "ok":
             by_n.setdefault(r.N, []).append(r.latency_s)
     out["p50_latency_s_by_N"] = {int(n): float(np.percentile(v, 50)) for n, v in sorted(by_n.items())}
+    if args.admit_window_s is not None:
+        out["admit_window_s"] = args.admit_window_s
     out["workload"] = (f"{args.requests} requests, Poisson arrivals at {args.rate} req/s over "
                        f"{arrivals[-1][0]:.1f} s, {args.slots} slots, budget {args.budget_gb} GB, mixed path "
                        f"(split-bf16 products, float64-class filter, float64-accurate smoothed-mean solve)")

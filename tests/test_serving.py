@@ -151,3 +151,33 @@ def test_request_solve_default_follows_the_precision():
     assert serve.Request(0, 0.0, p).solve_prec == B.KF_SOLVE_FP64_MEAN
     assert serve.Request(0, 0.0, p, prec=B.KF_PREC_FP64).solve_prec == B.KF_SOLVE_FP32
     assert serve.Request(0, 0.0, p, solve_prec=B.KF_SOLVE_FP64_TC).solve_prec == B.KF_SOLVE_FP64_TC
+
+
+def test_admission_window_and_progress(monkeypatch):
+    """Requests still waiting when the admission window closes are reported as not admitted; the
+    admitted ones finish; progress sees the results while the run goes on (fake worker, no GPU)."""
+    import time as _time
+
+    def fake_worker(self, req, res, budget, t0):
+        _time.sleep(0.05)
+        res.finished_s = _time.perf_counter() - t0
+        with self._cv:
+            self._in_use -= res.charged_bytes
+            self._active -= 1
+            self._cv.notify_all()
+
+    monkeypatch.setattr(serve.Server, "_worker", fake_worker)
+    monkeypatch.setattr(serve, "plan_bytes", lambda prob, req, budget: (0, 1000, 1))
+    reqs = [serve.Request(i, 0.0 if i < 3 else 5.0, serve.LazyProblem(64, 8, 3, identity_F=True, seed=i))
+            for i in range(6)]
+    seen = []
+    res = serve.Server(budget_bytes=10 ** 9, max_slots=1, use_arena=False).run(
+        reqs, admit_until_s=0.12, progress=lambda rs: seen.append(sum(r.finished_s > 0 for r in rs)),
+        progress_every_s=0.0)
+    done = [r for r in res if r.status == "ok"]
+    late = [r for r in res if r.status.startswith("not admitted")]
+    assert 1 <= len(done) <= 3 and len(done) + len(late) == 6
+    assert all(r.rid >= len(done) for r in late) and all(r.finished_s > 0 for r in done)
+    assert seen and max(seen) <= len(done)
+    summary = serve.summarize(res, 1.0)
+    assert summary["completed"] == len(done) and summary["not_admitted"] == len(late)
