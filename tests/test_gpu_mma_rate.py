@@ -1,8 +1,10 @@
 """Issue rate of the tcgen05 MMA shapes the kernels use (tests/gpu_mma_rate.cu, built with nvcc for
-sm_103a): cycles per 128 x N x 16 bf16 MMA for N = 64, 128, 256.  The exact-slice kernel's tile width
-(N = 64, one 64-column TMEM accumulator per slice level) is bounded by the N = 64 rate; the split-bf16
-kernel uses N = 256.  The measured figures are printed; the test checks that every launch completed
-(no timeout, no CUDA error) and that the per-clock rate does not fall as N grows."""
+sm_103a): cycles per 128 x N x 16 bf16 MMA for N = 64, 128, 256.  N = 64 reads its operands from
+shared memory at the full shared-memory rate and runs at two thirds of the bf16 rate, so the
+exact-slice kernel issues one MMA per run of up to four slice levels whose 64-column TMEM accumulators
+are adjacent (N up to 256); the split-bf16 kernel uses N = 256.  The measured figures are printed; the
+test checks that every launch completed (no timeout, no CUDA error) and that the per-clock rate does
+not fall as N grows."""
 import os
 import re
 import shutil
