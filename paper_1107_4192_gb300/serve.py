@@ -166,11 +166,16 @@ class Server:
         self._cv = threading.Condition(self._lock)
         self._in_use = 0
         self._active = 0
+        self._arena_active = False
 
     def _charge(self, prob, req):
         """(bytes to reserve now, plan budget): bytes None = wait, -1 = never fits."""
         inputs = input_bytes(prob)
         free = self.budget - self._in_use - inputs
+        if self._arena_active:
+            # plans take their memory from the arena, whose free space the blocks of finished plans
+            # can leave fragmented: a plan whose bytes fit in the largest free block always fits
+            free = min(free, B.kf_arena_stats()[2])
         need_full = admission_footprint(prob.N, prob.T)
         st, full_bytes, c = plan_bytes(prob, req, 0)
         if max(need_full, full_bytes) <= free:
@@ -231,6 +236,7 @@ class Server:
                 arena = True
             except B.KfError:
                 arena = False
+        self._arena_active = arena
         t0 = time.perf_counter()
         pending: List[Request] = []
         i = 0
@@ -280,6 +286,7 @@ class Server:
         for th in threads:
             th.join()
         if arena:
+            self._arena_active = False
             B.kf_arena_release()
         return [results[r.rid] for r in reqs]
 

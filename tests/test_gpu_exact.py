@@ -71,7 +71,7 @@ def exact_sliced_product(A, Bm, L):
 
 
 @pytest.mark.parametrize("levels", [4, 5, 6, 7])
-@pytest.mark.parametrize("M,N,K", [(130, 70, 300), (256, 192, 1024), (1, 1, 1), (129, 65, 33)])
+@pytest.mark.parametrize("M,N,K", [(130, 70, 300), (256, 192, 1024), (1, 1, 1), (129, 65, 33), (70, 130, 3000)])
 def test_exact_product_matches_the_scheme(levels, M, N, K):
     rng = np.random.default_rng(M + N + K + levels)
     A = rng.standard_normal((M, K)) * np.exp(rng.uniform(-4, 4, (M, 1))) * np.exp(rng.uniform(-3, 3, (M, K)))
@@ -175,3 +175,29 @@ def test_exact_product_non_finite_rows_give_nan():
     bad = np.zeros(M, bool)
     bad[[3, 9]] = True
     assert np.all(np.isnan(got[bad])) and np.all(np.isfinite(got[~bad]))
+
+
+def test_exact_product_wait_limit_timeout_then_recovery():
+    """Failure detection of the exact-slice pipeline without a fault: with the pipeline waits
+    limited to 1 ns the gate, MMA, TMA and epilogue roles stop at their first unmet wait, the
+    kernel waits for what it already issued, frees its tensor memory and the entry point returns
+    KF_ERR_TIMEOUT; with the default limit restored the same call matches the scheme."""
+    rng = np.random.default_rng(11)
+    M, N, K = 256, 128, 2048
+    A = rng.standard_normal((M, K))
+    Bm = rng.standard_normal((N, K))
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(Bm).cuda()
+    C = torch.zeros(M, N, dtype=torch.float64, device="cuda")
+    prev = B.kfx_tc_wait_limit(1)
+    try:
+        for _ in range(2):
+            with pytest.raises(B.KfError) as e:
+                B.kfx_gemm_exact(7, M, N, K, 1.0, dA, K, dB, K, 0.0, 0.0, C, N)
+            assert e.value.status == B.KF_ERR_TIMEOUT
+    finally:
+        B.kfx_tc_wait_limit(0)
+    assert prev == 2_000_000_000
+    B.kfx_gemm_exact(7, M, N, K, 1.0, dA, K, dB, K, 0.0, 0.0, C, N)
+    ref, ea, eb = exact_sliced_product(A, Bm, 7)
+    scale = np.ldexp(1.0, (ea[:, None] + eb[None, :]).astype(np.int64))
+    assert np.all(np.abs(C.cpu().numpy() - ref) <= 2.0 ** -50 * scale + 4 * np.spacing(np.abs(ref)))

@@ -181,3 +181,22 @@ def test_admission_window_and_progress(monkeypatch):
     assert seen and max(seen) <= len(done)
     summary = serve.summarize(res, 1.0)
     assert summary["completed"] == len(done) and summary["not_admitted"] == len(late)
+
+
+def test_charge_respects_the_arena_largest_free_block(built, monkeypatch):
+    """With plans in the arena, admission is bounded by its largest free block, not by the free
+    total: a fragmented arena puts a request in recompute mode or makes it wait."""
+    prob = synth.random_walk_problem(512, 32, 40, seed=1)
+    req = serve.Request(0, 0.0, prob)
+    full = serve.plan_bytes(prob, req, 0)[1]
+    srv = serve.Server(budget_bytes=10 * full, max_slots=2)
+    srv._arena_active = True
+    monkeypatch.setattr(B, "kf_arena_stats", lambda: (10 * full, 0, 10 * full))
+    charge, budget = srv._charge(prob, req)
+    assert budget == 0 and charge >= full                       # contiguous space: full store
+    monkeypatch.setattr(B, "kf_arena_stats", lambda: (10 * full, 0, int(0.7 * full)))
+    charge, budget = srv._charge(prob, req)
+    assert charge is not None and 0 < budget <= int(0.7 * full)  # fragmented: checkpointed
+    assert serve.plan_bytes(prob, req, budget)[1] <= int(0.7 * full)
+    monkeypatch.setattr(B, "kf_arena_stats", lambda: (10 * full, 0, 1000))
+    assert srv._charge(prob, req)[0] is None                      # nothing fits now: wait
