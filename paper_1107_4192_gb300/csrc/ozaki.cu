@@ -36,7 +36,8 @@ constexpr int OZ_BM = 128;      // output rows per CTA (TMEM lanes)
 constexpr int OZ_BN = 64;       // output columns per CTA (TMEM columns per level)
 constexpr int OZ_KC = 128;      // values of k per exact chunk
 constexpr int OZ_EPI_WARPS = 16;  // 4 TMEM lane quadrants x 4 column quarters of 16
-constexpr int OZ_THREADS = 32 * (2 + OZ_EPI_WARPS);
+constexpr int OZ_GATE_WARP = 2 + OZ_EPI_WARPS;  // waits for each k-step's operands and buffer
+constexpr int OZ_THREADS = 32 * (3 + OZ_EPI_WARPS);
 constexpr int OZ_GROUP = 8;     // row tiles per rasterisation group (operand reuse in L2)
 constexpr int OZ_ROW_PAD = 128;
 constexpr int kOzBK = 32;       // k per pipeline stage of the launched kernels (two MMA k-steps)
@@ -271,14 +272,17 @@ __device__ __forceinline__ void oz_drain(uint32_t taddr, uint32_t dbar, int lane
 // run whose buffers pass the last one (known from cm at run time) is issued as two MMAs.  The level
 // LS that starts a chunk at this k-step gets its own MMA at pa = 0, the chunk's first, which
 // overwrites the accumulator instead of adding to it (at the first k-step every level starts, and
-// all of pa = 0's MMAs overwrite).
-template <int LV, int BK, int R>
+// all of pa = 0's MMAs overwrite).  `pre` runs after the MMAs of the first A slices, about half
+// of the k-step's work.
+template <int LV, int BK, int R, typename Pre>
 __device__ __forceinline__ void oz_issue_kstep(bool leader, uint32_t tmem, uint64_t adesc0, uint64_t bdesc0, int cm,
-                                               bool first_step) {
+                                               bool first_step, Pre&& pre) {
   using C = OzCfg<LV, BK>;
   constexpr int LS = R == 0 ? 0 : C::CKS - R;
+  constexpr int PRE_AFTER = LV >= 5 ? 2 : 1;
 #pragma unroll
   for (int pa = 0; pa < LV; ++pa) {
+    if (pa == PRE_AFTER) pre();
     int l0 = pa;
 #pragma unroll
     for (int l = pa + 1; l <= LV; ++l) {
@@ -300,6 +304,29 @@ __device__ __forceinline__ void oz_issue_kstep(bool leader, uint32_t tmem, uint6
         l0 = l;
       }
     }
+  }
+}
+
+// The gate counter: the number of k-steps whose operands have landed and whose starting level's
+// buffer has been drained (written by the gate warp with release, read by the MMA warp with acquire).
+__device__ __forceinline__ uint32_t oz_gate_load(uint32_t addr) {
+  uint32_t v;
+  asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+  return v;
+}
+__device__ __forceinline__ void oz_gate_store(uint32_t addr, uint32_t v) {
+  asm volatile("st.release.cta.shared::cta.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+// Bounded wait until the gate passes k-step t; false on timeout or abort.
+__device__ __forceinline__ bool oz_gate_wait(uint32_t addr, uint32_t t, volatile int* abort_flag, uint64_t limit_ns,
+                                             uint32_t& gate) {
+  gate = oz_gate_load(addr);
+  if (gate > t) return true;
+  const uint64_t t0 = globaltimer();
+  for (;;) {
+    gate = oz_gate_load(addr);
+    if (gate > t) return true;
+    if (*abort_flag || globaltimer() - t0 > limit_ns) return false;
   }
 }
 
@@ -331,6 +358,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
       reinterpret_cast<uint32_t*>(gbase + C::STAGES * C::STAGE_BYTES + 8 * (2 * C::STAGES + 2 * C::NB + 1));
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   volatile int* skip_flag = reinterpret_cast<volatile int*>(tmem_slot + 2);
+  const uint32_t gate_addr = smem_u32(tmem_slot + 3);  // k-steps released to the MMA warp
   volatile int never = 0;  // abort flag of the clean-up waits, which must not stop early
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -346,6 +374,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
     mbar_init(done_bar, 1);
     *abort_flag = 0;
     *skip_flag = status_failed(a.e.status) ? 1 : 0;
+    tmem_slot[3] = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -391,82 +420,112 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
   } else if (warp == 1) {
     // ---------------- MMA issuer: the whole warp runs the loop, so the stage, buffer and descriptor
     // arithmetic is warp-uniform; one elected lane issues.  TMEM buffer b = columns [64 b, 64 b + 64).
-    // Level l's exact chunks are staggered by l k-steps (chunk k covers k-steps [k CKS - l,
-    // (k + 1) CKS - l)), so at most one level starts a chunk per k-step, and chunk k of level l
-    // accumulates in buffer (l + k) mod NB.  That buffer last held chunk k - 1 of level l + 1, which
-    // ended two k-steps earlier: its drain has a full k-step of MMAs to finish.
+    // The gate warp tells it which k-steps may start (operands landed, new buffer drained); the
+    // MMA queue is shallow, so the issuer does no barrier test of its own between k-steps: it reads
+    // the gate counter half-way through each k-step's MMAs, and that load's latency overlaps them.
     leader = elect_one();
     bool ok = true;
-    uint32_t used = 0, par = 0;  // per buffer: used before; parity of its uses so far
+    uint32_t gate = 0;  // k-steps released so far (last value read)
+    const int nks = nk * C::KS;
     for (int it = 0; it < nk && ok; ++it) {
       const int s = it % C::STAGES;
-      const uint32_t ph = (uint32_t)(it / C::STAGES) & 1u;
-      ok = __all_sync(0xffffffffu, mbar_wait(full_bar(s), ph, abort_flag, a.wait_ns));
-      if (!ok) {
-        if (lane == 0) {
-          *abort_flag = 1;
-          status_set(a.e.status, KF_ERR_TIMEOUT, a.e.step, 12);
-        }
-        break;
-      }
       const uint32_t st = base + s * C::STAGE_BYTES;
       const uint64_t adesc_s = smem_desc_sw(st, C::SBO, C::LAYOUT);
       const uint64_t bdesc_s = smem_desc_sw(st + LV * C::A_BYTES, C::SBO, C::LAYOUT);
 #pragma unroll
       for (int j = 0; j < C::KS; ++j) {
         const int t = it * C::KS + j;  // k-step
+        if (gate <= (uint32_t)t) {
+          ok = __all_sync(0xffffffffu, oz_gate_wait(gate_addr, (uint32_t)t, abort_flag, a.wait_ns, gate));
+          gate = __shfl_sync(0xffffffffu, gate, 0);
+          if (!ok) {
+            if (lane == 0 && !*abort_flag) {
+              *abort_flag = 1;
+              status_set(a.e.status, KF_ERR_TIMEOUT, a.e.step, 12);
+            }
+            break;
+          }
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const int ck = t / C::CKS, r = t - ck * C::CKS, cm = ck % C::NB;
         auto buf = [&](int l) {  // buffer of level l at this k-step
           const int b = l + cm + (l >= C::CKS - r ? 1 : 0);
           return b >= C::NB ? b - C::NB : b;
         };
-        // the one level that starts a chunk here ((t + l) % CKS == 0; every level at the first
-        // k-step, in fresh buffers) waits until its buffer has been drained
-        if (t == 0) {
-          used = par = (1u << LV) - 1u;
-        } else {
-          const int ls = r == 0 ? 0 : C::CKS - r;
-          if (ls < LV) {
-            const int b = buf(ls);
-            if ((used >> b) & 1u) {
-              ok = __all_sync(0xffffffffu, mbar_wait(drained_bar(b), ((par >> b) & 1u) ^ 1u, abort_flag, a.wait_ns));
-              if (!ok) {
-                if (lane == 0) {
-                  *abort_flag = 1;
-                  status_set(a.e.status, KF_ERR_TIMEOUT, a.e.step, 13);
-                }
-                break;
-              }
-            }
-            used |= 1u << b;
-            par ^= 1u << b;
-          }
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        uint32_t gate_ahead = gate;
+        auto pre = [&]() { gate_ahead = oz_gate_load(gate_addr); };
         // k-step j reads the next 32 bytes of every swizzled row (start address in 16-byte units)
         const uint64_t adesc0 = adesc_s + (uint64_t)(2 * j), bdesc0 = bdesc_s + (uint64_t)(2 * j);
         switch (r) {
-          case 0: oz_issue_kstep<LV, BK, 0>(leader, tmem, adesc0, bdesc0, cm, t == 0); break;
-          case 1: oz_issue_kstep<LV, BK, 1>(leader, tmem, adesc0, bdesc0, cm, t == 0); break;
-          case 2: oz_issue_kstep<LV, BK, 2>(leader, tmem, adesc0, bdesc0, cm, t == 0); break;
-          case 3: oz_issue_kstep<LV, BK, 3>(leader, tmem, adesc0, bdesc0, cm, t == 0); break;
-          case 4: oz_issue_kstep<LV, BK, 4>(leader, tmem, adesc0, bdesc0, cm, t == 0); break;
-          case 5: oz_issue_kstep<LV, BK, 5>(leader, tmem, adesc0, bdesc0, cm, t == 0); break;
-          case 6: oz_issue_kstep<LV, BK, 6>(leader, tmem, adesc0, bdesc0, cm, t == 0); break;
-          default: oz_issue_kstep<LV, BK, 7>(leader, tmem, adesc0, bdesc0, cm, t == 0); break;
+          case 0: oz_issue_kstep<LV, BK, 0>(leader, tmem, adesc0, bdesc0, cm, t == 0, pre); break;
+          case 1: oz_issue_kstep<LV, BK, 1>(leader, tmem, adesc0, bdesc0, cm, t == 0, pre); break;
+          case 2: oz_issue_kstep<LV, BK, 2>(leader, tmem, adesc0, bdesc0, cm, t == 0, pre); break;
+          case 3: oz_issue_kstep<LV, BK, 3>(leader, tmem, adesc0, bdesc0, cm, t == 0, pre); break;
+          case 4: oz_issue_kstep<LV, BK, 4>(leader, tmem, adesc0, bdesc0, cm, t == 0, pre); break;
+          case 5: oz_issue_kstep<LV, BK, 5>(leader, tmem, adesc0, bdesc0, cm, t == 0, pre); break;
+          case 6: oz_issue_kstep<LV, BK, 6>(leader, tmem, adesc0, bdesc0, cm, t == 0, pre); break;
+          default: oz_issue_kstep<LV, BK, 7>(leader, tmem, adesc0, bdesc0, cm, t == 0, pre); break;
         }
         __syncwarp();
         mma_issued = true;
         if (leader) {  // the level whose chunk ends here (every level at the last k-step) is ready
 #pragma unroll
           for (int l = 0; l < LV; ++l)
-            if ((t + l) % C::CKS == C::CKS - 1 || t == nk * C::KS - 1) mma_commit(ready_bar(buf(l)));
+            if ((t + l) % C::CKS == C::CKS - 1 || t == nks - 1) mma_commit(ready_bar(buf(l)));
         }
-        __syncwarp();
+        gate = __shfl_sync(0xffffffffu, max(gate, gate_ahead), 0);
       }
       if (!ok) break;
       if (leader) mma_commit(empty_bar(s));
       __syncwarp();
+    }
+  } else if (warp == OZ_GATE_WARP) {
+    // ---------------- gate: per k-step, wait (bounded) for its stage's operands (at the stage's
+    // first k-step) and, when a level starts a chunk there in a buffer used before, for that
+    // buffer's drain; then release the k-step to the MMA warp.  Level l's exact chunks are
+    // staggered by l k-steps (chunk k covers k-steps [k CKS - l, (k + 1) CKS - l)), so at most one
+    // level starts a chunk per k-step, and chunk k of level l accumulates in buffer (l + k) mod NB.
+    // That buffer last held chunk k - 1 of level l + 1, which ended two k-steps earlier: its drain
+    // has a full k-step of MMAs to finish.
+    uint32_t used = 0, par = 0;  // per buffer: used before; parity of its uses so far
+    const int nks = nk * C::KS;
+    for (int t = 0; t < nks; ++t) {
+      const int it = t / C::KS;
+      if (t == it * C::KS) {
+        const int s = it % C::STAGES;
+        const uint32_t ph = (uint32_t)(it / C::STAGES) & 1u;
+        if (!__all_sync(0xffffffffu, mbar_wait(full_bar(s), ph, abort_flag, a.wait_ns))) {
+          if (lane == 0 && !*abort_flag) {
+            *abort_flag = 1;
+            status_set(a.e.status, KF_ERR_TIMEOUT, a.e.step, 15);
+          }
+          break;
+        }
+      }
+      const int ck = t / C::CKS, r = t - ck * C::CKS, cm = ck % C::NB;
+      if (t == 0) {
+        used = par = (1u << LV) - 1u;
+      } else {
+        const int ls = r == 0 ? 0 : C::CKS - r;
+        if (ls < LV) {
+          int b = ls + cm + 1;  // the starting level has moved on: (ls + (t + ls) / CKS) mod NB
+          if (r == 0) b = cm;
+          if (b >= C::NB) b -= C::NB;
+          if ((used >> b) & 1u) {
+            if (!__all_sync(0xffffffffu, mbar_wait(drained_bar(b), ((par >> b) & 1u) ^ 1u, abort_flag, a.wait_ns))) {
+              if (lane == 0 && !*abort_flag) {
+                *abort_flag = 1;
+                status_set(a.e.status, KF_ERR_TIMEOUT, a.e.step, 13);
+              }
+              break;
+            }
+          }
+          used |= 1u << b;
+          par ^= 1u << b;
+        }
+      }
+      __syncwarp();
+      if (lane == 0) oz_gate_store(gate_addr, (uint32_t)(t + 1));
     }
   } else if (warp >= 2) {
     // ---------------- epilogue: exact level sums into 64-bit fixed point, then scale and store
