@@ -373,8 +373,8 @@ def main():
     avg_s = ms_l / 1e3 / max(n_l, 1)
     achieved = smoother_gemm_flops_per_launch(N) / avg_s / 1e12
     # DRAM bytes of one launch of that kernel at N = 8196 (dram__bytes_read.sum + dram__bytes_write.sum,
-    # one ncu --set full capture of W = J D at t = 2 of the T = 3 run: 4.280e9 read + 0.278e9 written)
-    traffic = 4.557e9 if args.prec == "mixed" and prof[7][0] > 0 and N == 8196 else None
+    # one ncu --set full capture of W = J D at t = 2 of the T = 3 run: 2.556e9 read + 0.280e9 written)
+    traffic = 2.836e9 if args.prec == "mixed" and prof[7][0] > 0 and N == 8196 else None
     roof.update({"kernel": kname, "achieved": achieved, "frac": achieved / roof["peak"], "traffic": traffic,
                  "peak_source": peak_src, "launches": n_l, "avg_launch_ms": avg_s * 1e3,
                  "work_per_launch": f"(2 N^3 + N^2 (N+1)) / 2 flops, N = {N}"})
@@ -408,7 +408,13 @@ def main():
                 "achieved": issued / t_x / 1e12, "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s",
                 "peak_source": peak_src,
                 "peak_note": "bf16_tflops_sustained (measured): the products are bf16 slice products",
-                "traffic": None, "launches": n_x, "avg_launch_ms": ms_x / max(n_x, 1),
+                # DRAM bytes of one oz_gemm_kernel<7> launch at N = 8196 (dram__bytes_read.sum +
+                # dram__bytes_write.sum, one ncu capture of the T = 3 run: 38.14e9 read + 0.56e9
+                # written); the 5-level launch streams 5/7 of the slice planes
+                "traffic": 38.70e9 if N == 8196 else None,
+                "traffic_note": "per oz_gemm_kernel<7> launch; the operand planes are re-read from DRAM by "
+                                "every 8-row-tile group (20x the 1.9 GB of planes), at 23% of HBM bandwidth",
+                "launches": n_x, "avg_launch_ms": ms_x / max(n_x, 1),
                 "work_per_launch": f"(15 or 28) x 2 N^3 bf16 flops, N = {N} (levels 5 and 7)",
                 "fp64_equivalent_tflops": launches_per_step * 2 * N ** 3 * steps_x / t_x / 1e12,
                 "fp64_equivalent_note": "2 N^3 float64-accurate flops per launch, vs 1.25 TFLOP/s nominal "
