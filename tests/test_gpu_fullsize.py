@@ -71,3 +71,30 @@ def test_fullsize_properties():
     P = out["P_smooth_at"]
     assert np.array_equal(P, P.T)
     assert np.allclose(np.diag(P), out["diagP_smooth"][1], rtol=0, atol=0)
+
+
+@pytest.mark.skipif(not __import__("os").environ.get("KFMEG_LONG"),
+                    reason="a whole float64 epoch at N = 8196 takes about 13 minutes; set KFMEG_LONG=1")
+def test_full_epoch_mixed_vs_fp64_gpu():
+    """The whole benchmark epoch (N = 8196, m = 306, T = 300, Joseph every 16 steps) on the mixed
+    path with the float64-accurate solve, against the float64 GPU path (oracle-checked at smaller
+    sizes and on the first steps at this size), within the mixed tolerances; prints both epoch
+    times (the float64 one is the plain-float64 baseline measured over the whole epoch)."""
+    import time
+    prob = synth.config2()
+    t0 = time.perf_counter()
+    ref = solver.run(prob, prec=B.KF_PREC_FP64)
+    torch.cuda.synchronize()
+    t_fp64 = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    out = solver.run(prob, joseph_every=16, **MIXED64)
+    torch.cuda.synchronize()
+    t_mix = time.perf_counter() - t0
+    e = {"x_filt": rel_err_per_step(out["x_filt"], ref["x_filt"]),
+         "x_smooth": rel_err_per_step(out["x_smooth"], ref["x_smooth"]),
+         "diagP_filt": rel_err_elementwise(out["diagP_filt"], ref["diagP_filt"]),
+         "diagP_smooth": rel_err_elementwise(out["diagP_smooth"], ref["diagP_smooth"])}
+    print(f"N=8196 m=306 T=300: float64 epoch {t_fp64:.1f} s ({prob.T / t_fp64:.3f} timesteps/s), mixed "
+          f"float64-accurate solve {t_mix:.1f} s (including upload and plan); errors vs float64 GPU path: {e}")
+    assert e["x_filt"] <= 1e-4 and e["x_smooth"] <= 1e-4
+    assert e["diagP_filt"] <= 1e-3 and e["diagP_smooth"] <= 1e-3
