@@ -46,7 +46,7 @@ typedef enum {
   KF_ERR_NUMERIC = 5,      /* NaN/Inf in data or a non-positive covariance diagonal */
   KF_ERR_TIMEOUT = 6,      /* a bounded device wait expired                        */
   KF_ERR_STATE = 7,        /* call order violated (fis_smooth before kf_filter)    */
-  KF_ERR_UNSUPPORTED = 8   /* combination not available in this build              */
+  KF_ERR_UNSUPPORTED = 8   /* combination the compiled library does not provide    */
 } kf_status;
 
 typedef enum { KF_F_IDENTITY = 0, KF_F_CSR = 1, KF_F_DENSE = 2 } kf_f_kind;

@@ -1336,7 +1336,7 @@ const char* kf_strerror(kf_status s) {
     case KF_ERR_NUMERIC: return "non-finite value or non-positive variance";
     case KF_ERR_TIMEOUT: return "bounded device wait expired";
     case KF_ERR_STATE: return "call order violated (fis_smooth needs a successful kf_filter)";
-    case KF_ERR_UNSUPPORTED: return "unsupported in this build";
+    case KF_ERR_UNSUPPORTED: return "unsupported by the compiled library";
   }
   return "unknown status";
 }

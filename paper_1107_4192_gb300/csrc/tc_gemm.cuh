@@ -34,7 +34,7 @@ extern thread_local TcLaunchTimer* g_tc_timer;
 extern std::atomic<uint64_t> g_tc_wait_ns;
 constexpr uint64_t kTcDefaultWaitNs = 2000000000ull;
 
-// True when this build carries the tcgen05 kernels.
+// True when the library was compiled with the tcgen05 kernels.
 bool tc_available();
 
 // 2-D TMA map of a bf16 matrix (rows x cols, leading dimension ld elements,
